@@ -1,0 +1,95 @@
+"""Seeded synthetic NNLS instances (inputs only; no solver arithmetic).
+
+The paper measures on a 548-matrix basis-pursuit dataset that is not
+available here; these generators stand in for it with dense, seeded
+instances of the shapes and value distributions used for the benchmarks:
+well-conditioned underdetermined sparse recovery (Gaussian A, sparse
+nonnegative x0, noiseless b) and dense overdetermined problems with noise.
+N(0, v) below means variance v.  Every matrix is returned as a column-major
+(Fortran-order) float64 array.  Both the CUDA path's tests/benchmark and the
+CPU oracle read the same arrays.
+"""
+import numpy as np
+
+
+def _sparse_nonneg(rng, n, s, lo=0.1):
+    """s nonzeros at random positions, values uniform on (lo, 1]."""
+    x = np.zeros(n)
+    idx = rng.choice(n, size=s, replace=False)
+    x[idx] = 1.0 - rng.uniform(0.0, 1.0 - lo, size=s)
+    return x
+
+
+def gaussian_recovery(m, n, s, seed, unit_columns=False):
+    """A ~ N(0, 1/m) (or unit-norm Gaussian columns), x0 >= 0 with s nonzeros
+    uniform on (0.1, 1], b = A x0 (noiseless)."""
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+    if unit_columns:
+        A /= np.linalg.norm(A, axis=0, keepdims=True)
+    x0 = _sparse_nonneg(rng, n, s)
+    b = A @ x0
+    return np.asfortranarray(A), b, x0
+
+
+def small_recovery(seed):
+    """256 x 512, entries N(0, 1/256), 25 nonzeros, noiseless."""
+    return gaussian_recovery(256, 512, 25, seed)
+
+
+def overdetermined_uniform(seed, m=4096, n=2048, noise_var=1e-4):
+    """A ~ U[0,1) (m x n), x_true with half its entries zero and the rest
+    uniform on (0, 1], b = A x_true + N(0, noise_var) noise."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0.0, 1.0, size=(m, n))
+    x = np.zeros(n)
+    nz = rng.choice(n, size=n - n // 2, replace=False)
+    x[nz] = 1.0 - rng.uniform(0.0, 1.0, size=nz.size)
+    b = A @ x + rng.normal(0.0, np.sqrt(noise_var), size=m)
+    return np.asfortranarray(A), b, x
+
+
+def sparse_recovery_sweep(seed, s, m=2048, n=8192):
+    """Gaussian A with unit-norm columns, x0 >= 0 with s nonzeros, noiseless."""
+    return gaussian_recovery(m, n, s, seed + 7919 * s, unit_columns=True)
+
+
+def batched_uneven(batch_seed=0, count=1024, m_lo=64, m_hi=512, density=0.1, noise_var=1e-3):
+    """`count` independent instances, m ~ U{m_lo..m_hi}, n = 2m, A ~ N(0, 1/m),
+    x0 with density*n nonzeros uniform on (0.1, 1], b = A x0 + N(0, noise_var).
+    Instance i is drawn from seed 1000 + i; its size from the batch seed."""
+    sizes = np.random.default_rng(batch_seed).integers(m_lo, m_hi + 1, size=count)
+    out = []
+    for i, m in enumerate(sizes):
+        m = int(m)
+        n = 2 * m
+        rng = np.random.default_rng(1000 + i)
+        A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+        x0 = _sparse_nonneg(rng, n, max(1, int(round(density * n))))
+        b = A @ x0 + rng.normal(0.0, np.sqrt(noise_var), size=m)
+        out.append((np.asfortranarray(A), b, x0))
+    return out
+
+
+def layer_batch(count=256, m=512, n=1024, s=40, noise_var=1e-3, seed0=0):
+    """Instances for the differentiable-layer workload: A ~ N(0, 1/m),
+    x0 with s nonzeros uniform on (0.1, 1], b = A x0 + N(0, noise_var),
+    x_target = x0 + 1e-2 * xi with xi ~ N(0, I)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+        x0 = _sparse_nonneg(rng, n, s)
+        b = A @ x0 + rng.normal(0.0, np.sqrt(noise_var), size=m)
+        x_target = x0 + 1e-2 * rng.normal(size=n)
+        out.append((np.asfortranarray(A), b, x0, x_target))
+    return out
+
+
+def tiny(seed, m, n, kind="gauss"):
+    """Small dense instances for brute-force checks: Gaussian A and a
+    Gaussian b (so the nonnegativity constraint is active)."""
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(m, n)) if kind == "gauss" else rng.uniform(size=(m, n))
+    b = rng.normal(size=m)
+    return np.asfortranarray(A), b
