@@ -1,0 +1,327 @@
+"""Benchmark: NNLS solves/s of LHDM vs one-column LH on one GB300.
+
+Workload (one "step" = one complete solve, every row of the hot path):
+dense overdetermined NNLS, A 4096 x 2048 with U[0,1) entries, half of x zero,
+b = A x + N(0, 1e-4) noise (seed 0), FP64.  The step is LHDM with k_max = 32
+(tau1 = 0.6, tau2 = 0.15, delta = 0.9); the one-column LH solve of the same
+instance on the same GPU is timed beside it.  A (64 MiB) fits in L2, so L2 is
+flushed (a 512 MiB device write) before every timed solve.
+
+Default arm: the CUDA path through the C ABI.  --impl reference: the CPU
+oracle (plain C, the checker of the tests) timed on the host cores.
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own copy
+(replicas; there is no data-path collective), the time is the max over ranks
+and value = the solves of all ranks per second.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NNLS solves/s: LHDM vs 1-col LH, same GB300, passive set exact, rel err<=1e-10"
+WORKLOAD = ("overdetermined dense NNLS, A 4096x2048 U[0,1), 50% zero x, nonzeros U(0,1], "
+            "b = A x + N(0,1e-4), seed 0, FP64")
+DFMA_PER_CLK_PER_SM = 2.0  # measured on this machine's GB300 (DFMA microbenchmark)
+
+
+def _oracle_solve(k_max):
+    """Runs in a spawned process: one oracle solve of the benchmark instance."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2108_05345_gb300 import workloads as WL
+    A, b, _ = WL.overdetermined_uniform(0)
+    t0 = time.perf_counter()
+    r = O.nnls(A, b, k_max=k_max)
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, x=r["x"].tolist(), passive=r["passive"].tolist(), n_outer=r["n_outer"],
+                status=r["status"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock, power and throttle reasons."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 ".bench_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return out
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=sm[len(sm) // 2] if sm else None,
+                   sm_max_mhz=float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def reference_arm(args):
+    """The CPU oracle timed on the host cores: each step is one complete
+    oracle solve of the benchmark instance; steps run in parallel on a
+    spawned pool (one core each)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = max(1, min(os.cpu_count() or 1, args.steps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        if args.warmup > 0:
+            pool.map(_oracle_solve, [args.kmax] * min(args.warmup, cores))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_solve, [args.kmax] * args.steps)
+        wall = time.perf_counter() - t0
+    value = args.steps / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "k_max": args.kmax, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d complete oracle LHDM solves of the benchmark instance, one per core" % args.steps},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "mean_solve_s": sum(r["seconds"] for r in res) / len(res),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def once(args):
+    """One solve (for ncu captures): the benchmark instance family at m x n."""
+    import torch
+    from paper_2108_05345_gb300 import lhdm, workloads as WL
+    A, b, _ = WL.overdetermined_uniform(0, m=args.m, n=args.n)
+    At = lhdm.colmajor(torch.from_numpy(A).cuda())
+    bt = torch.from_numpy(b).cuda()
+    ctx = lhdm.Context(args.m, args.n)
+    x, p, info = ctx.solve(At, bt, lhdm.default_params(k_max=args.kmax))
+    torch.cuda.synchronize()
+    print(json.dumps({"once": True, "m": args.m, "n": args.n, "k_max": args.kmax, "info": info}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lhdm", choices=["lhdm", "reference"])
+    ap.add_argument("--kmax", type=int, default=32)
+    ap.add_argument("--lh-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and parity leg")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling mode: exactly one solve of the benchmark instance, no warm-up")
+    ap.add_argument("--m", type=int, default=4096, help="rows of the instance (--once only)")
+    ap.add_argument("--n", type=int, default=2048, help="columns of the instance (--once only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.once:
+        return once(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU leg starts first, in a spawned process (before any CUDA call)
+    cpu_job = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        pool = mp.get_context("spawn").Pool(1)
+        cpu_job = pool.apply_async(_oracle_solve, (args.kmax,))
+
+    import numpy as np
+    import torch
+    from paper_2108_05345_gb300 import lhdm, workloads as WL
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    A, b, _ = WL.overdetermined_uniform(0)
+    m, n = A.shape
+    dev = torch.device("cuda", local)
+    At = lhdm.colmajor(torch.from_numpy(A).to(dev))
+    bt = torch.from_numpy(b).to(dev)
+    ctx = lhdm.Context(m, n)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    prm = lhdm.default_params(k_max=args.kmax)
+    prm_lh = lhdm.default_params(k_max=1)
+
+    def timed(params, steps):
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.solve(At, bt, params, sync=False)
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in ts]
+
+    # warm-up, then the timed LHDM steps with clocks sampled meanwhile
+    timed(prm, max(3, args.warmup))
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_lhdm = timed(prm, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    x, p, info = ctx.solve(At, bt, prm)
+    ms_ph, fl_ph = ctx.profile()
+    trace = ctx.trace()
+    ms = float(np.mean(t_lhdm))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * 1000.0 / ms
+
+    # one-column LH on the same GPU
+    timed(prm_lh, 1)
+    t_lh = timed(prm_lh, args.lh_steps)
+    x_lh, p_lh, info_lh = ctx.solve(At, bt, prm_lh)
+    ms_lh = float(np.mean(t_lh))
+
+    # end to end: host buffers through lhdm_solve_host (copies inside)
+    Ah = torch.from_numpy(np.asfortranarray(A).T.copy()).pin_memory()  # column-major bytes
+    bh = torch.from_numpy(b.copy()).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    ph = torch.empty(n, dtype=torch.int32).pin_memory()
+    ctx.solve_host_ptr(m, n, Ah.data_ptr(), m, bh.data_ptr(), xh.data_ptr(), ph.data_ptr(), prm)
+    e2e_ts = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_host_ptr(m, n, Ah.data_ptr(), m, bh.data_ptr(), xh.data_ptr(), ph.data_ptr(), prm)
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_ts))
+
+    if rank != 0:
+        return 0
+
+    # roofline of the solve kernel (FP64-ALU bound) and of its dual GEMV phase
+    sm_mhz_peak = 2070.0
+    try:
+        mp_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(mp_json.get("hbm_gbs", 6791.4))
+        sm_mhz_peak = float(mp_json.get("sm_max_mhz", 2070.0))
+        hbm_src = "measured"
+    except Exception:
+        hbm, hbm_src = 6800.0, "fallback"
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_peak = DFMA_PER_CLK_PER_SM * 2.0 * nsm * sm_mhz_peak * 1e6 / 1e12  # TFLOP/s
+    flops_total = sum(fl_ph.values())
+    kernel_ms = float(np.median(t_lhdm))
+    achieved = flops_total / (kernel_ms * 1e-3) / 1e12
+    nZ_bytes = fl_ph["dual"] / 2.0 * 8.0 if fl_ph["dual"] else 0.0  # 8 bytes of A per FMA
+    dual_gbs = nZ_bytes / (ms_ph["dual"] * 1e-3) / 1e9 if ms_ph["dual"] > 0 else None
+
+    # parity against the CPU oracle (same instance, same parameters)
+    x_np, p_np = x.cpu().numpy(), p.cpu().numpy()
+    parity = None
+    cpu_baseline = None
+    if cpu_job is not None:
+        ref = cpu_job.get()
+        xr = np.array(ref["x"])
+        Pg = p_np[p_np >= 0].tolist()
+        rel = float(np.linalg.norm(x_np - xr) / np.linalg.norm(xr))
+        xl = x_lh.cpu().numpy()
+        pl = p_lh.cpu().numpy()
+        parity = {"passive_exact": Pg == ref["passive"], "rel_err": rel,
+                  "lh_passive_exact": pl[pl >= 0].tolist() == ref["passive"],
+                  "lh_rel_err": float(np.linalg.norm(xl - xr) / np.linalg.norm(xr)),
+                  "oracle_outer": ref["n_outer"], "gpu_outer": int(info["n_outer"])}
+        cpu_baseline = {"value": 1.0 / ref["seconds"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                        "sample": "one complete oracle LHDM (k_max=%d) solve of the benchmark instance (%.1f s)"
+                                  % (args.kmax, ref["seconds"])}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "k_max": args.kmax, "tau1": 0.6, "tau2": 0.15, "delta": 0.9,
+                   "l2": "flushed before every timed solve (512 MiB device write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU, one persistent launch per solve"},
+        "lh": {"value": world * 1000.0 / ms_lh, "unit": "solves/s", "ms_per_step": ms_lh,
+               "n_outer": int(info_lh["n_outer"]), "steps": args.lh_steps},
+        "speedup_vs_lh": ms_lh / ms,
+        "solve": {k: info[k] for k in ("status", "n_outer", "n_inner", "n_drop", "n_passive")},
+        "parity": parity,
+        "roofline": {"bound": "alu", "kernel": "lhdm_solve_grid_kernel", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "peak_source": "derived: %.0f DFMA/clk/SM (measured) x %d SMs x %.0f MHz"
+                                    % (DFMA_PER_CLK_PER_SM, nsm, sm_mhz_peak),
+                     "algorithmic_flops": flops_total, "traffic": None},
+        "dual_gemv": {"achieved_gbs": dual_gbs, "hbm_peak_gbs": hbm, "hbm_source": hbm_src,
+                      "frac_of_hbm": (dual_gbs / hbm) if dual_gbs else None,
+                      "fp64_frac": ((fl_ph["dual"] / (ms_ph["dual"] * 1e-3) / 1e12) / fp64_peak) if ms_ph["dual"] else None},
+        "phases_ms": {k: round(v, 4) for k, v in ms_ph.items()},
+        "cpu_baseline": cpu_baseline,
+        "e2e": {"value": 1.0 / e2e_s * world, "unit": "solves/s",
+                "h2d_bytes_per_step": 8 * m * n + 8 * m, "d2h_bytes_per_step": 8 * n + 4 * n + 48},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

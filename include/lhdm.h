@@ -1,0 +1,231 @@
+/*
+ * lhdm.h -- C ABI of the GB300 (sm_103a) FP64 solver for dense nonnegative
+ * least squares by Lawson-Hanson with Deviation Maximization (LHDM).
+ *
+ *   minimise ||A x - b||_2  subject to  x >= 0                  (problem (1))
+ *
+ * Method: Algorithm 3 of "The Lawson-Hanson Algorithm with Deviation
+ * Maximization: Finite Convergence and Sparse Recovery" (Dessole, Dell'Orto,
+ * Marcuzzi), with Algorithm 2 (DM) choosing up to k_max columns per outer
+ * step, Householder updating (Algorithm 4) of the partial QR factorisation
+ * Q^T A Pi = [R B; 0 C] (section 2.1) applied to the whole matrix, and
+ * Givens downdating (Algorithm 5) in the inner loop.  k_max = 1 is the
+ * one-column Lawson-Hanson method (Algorithm 1).  Every step runs in CUDA
+ * kernels on the device; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *  - All matrices are column-major FP64.  A is m x n with leading dimension
+ *    lda >= max(1, m).  Vectors are contiguous FP64 (int32 for index lists).
+ *  - "device" pointers must point to device memory the caller owns and keeps
+ *    alive until the stream work of the call has completed; "host" pointers
+ *    are ordinary host memory.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work on that stream, except where a
+ *    host-side result is documented: those calls synchronise the stream.
+ *  - Return value: LHDM_OK (0) or one of the LHDM_ERR_* codes below.  No call
+ *    aborts, throws or traps; CUDA errors are reported as LHDM_ERR_CUDA.
+ *  - Numerical status of a solve (iteration cap, non-finite input, ...) is
+ *    reported in lhdm_info.status; the call itself still returns LHDM_OK when
+ *    the work was enqueued and completed.
+ *  - Not thread-safe per context: calls on one lhdm_ctx must be serialised
+ *    by the caller.  Distinct contexts are independent.
+ */
+#ifndef LHDM_H
+#define LHDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status / error codes. */
+#define LHDM_OK 0
+#define LHDM_ERR_INVALID_ARG 1 /* bad size, pointer or parameter             */
+#define LHDM_ERR_MAX_ITER 2    /* outer-iteration cap reached (info.status)  */
+#define LHDM_ERR_NONFINITE 4   /* NaN/Inf in A or b (info.status)            */
+#define LHDM_ERR_CUDA 5        /* a CUDA runtime call failed                 */
+#define LHDM_ERR_TIMEOUT 6     /* a device-side wait exceeded its bound      */
+#define LHDM_ERR_ALLOC 7       /* device or host allocation failed           */
+#define LHDM_ERR_NO_STATE 8    /* backward called without a matching solve   */
+
+/* Largest supported block size k_max (columns chosen per outer step). */
+#define LHDM_KMAX_LIMIT 64
+
+/*
+ * Algorithm parameters (Algorithm 2 and Algorithm 3).
+ *  tau1, tau2 in (0, 1]: candidate thresholds on the dual vector w and on
+ *      the trailing column norms u (Algorithm 2, candidate set I).
+ *  delta in (0, 1]: bound on the absolute cosine between chosen projected
+ *      columns (Algorithm 2; Algorithm 3 names it tau_c in its signature).
+ *  k_max in [1, LHDM_KMAX_LIMIT]: at most k_max columns enter per outer step;
+ *      k_max = 1 is Lawson-Hanson (Algorithm 1).
+ *  tol_w: the outer loop stops when max over Z of w <= tol_w (the test
+ *      "max w > 0" of Algorithms 1 and 3 with a floating-point tolerance);
+ *      tol_w < 0 selects 10 * 2^-52 * max(m,n) * max_j ||a_j|| * ||b||.
+ *  max_outer: cap on outer iterations; <= 0 selects 3n.
+ * Defaults (lhdm_default_params): tau1 = 0.6, tau2 = 0.15, delta = 0.9,
+ * k_max = 32, the values of section 5.
+ */
+typedef struct {
+  double tau1;
+  double tau2;
+  double delta;
+  double tol_w;
+  int32_t k_max;
+  int32_t max_outer;
+} lhdm_params;
+
+/* Per-solve report. */
+typedef struct {
+  int32_t status;       /* LHDM_OK, LHDM_ERR_MAX_ITER, LHDM_ERR_NONFINITE,
+                           LHDM_ERR_TIMEOUT                                  */
+  int32_t n_outer;      /* outer iterations                                  */
+  int32_t n_inner;      /* inner-loop iterations (step-length/removal steps) */
+  int32_t n_drop;       /* columns dropped by the feasibility loop           */
+  int32_t n_passive;    /* |P| at exit                                       */
+  int32_t rank_limited; /* 1 if columns with w > tol_w were left out because
+                           their trailing norm was <= 100 eps ||a_j||        */
+  double resid_norm;    /* ||b - A x||                                       */
+  double max_wZ;        /* max over Z of w = A^T (b - A x) at exit           */
+  double tol_w;         /* tolerance actually used                           */
+} lhdm_info;
+
+typedef struct lhdm_ctx lhdm_ctx;
+typedef struct lhdm_batch lhdm_batch;
+
+/* Fills *p with the defaults listed above.  p: host. */
+int lhdm_default_params(lhdm_params* p);
+
+/* Short English description of a status code (static storage). */
+const char* lhdm_status_string(int status);
+
+/*
+ * Creates a single-solve context for problems up to max_m x max_n on the
+ * current CUDA device.  Allocates all device workspace here (FP64 about
+ * 8 * (max_m * max_n + min(max_m,max_n)^2) bytes plus O(max_m + max_n));
+ * later solves allocate nothing.  *ctx receives the handle (host).
+ * Errors: INVALID_ARG (sizes < 1 or ctx NULL), ALLOC, CUDA.
+ */
+int lhdm_create(lhdm_ctx** ctx, int32_t max_m, int32_t max_n);
+
+/* Releases the context and its device memory (synchronises the device). */
+int lhdm_destroy(lhdm_ctx* ctx);
+
+/*
+ * lhdm_solve: one NNLS problem, all steps on the device in one persistent
+ * cooperative launch over every SM (Algorithm 3; Algorithm 1 if k_max = 1).
+ *  m, n        problem size, 0 <= m <= max_m, 0 <= n <= max_n of the context.
+ *  A           device, m x n, column-major, leading dimension lda.
+ *  b           device, length m.
+ *  prm         host; NULL selects the defaults.
+ *  x           device, length n: the solution (x_Z = 0).
+ *  passive     device, length n: the passive set P sorted ascending, then -1.
+ *  info        host or NULL.  When non-NULL the call synchronises the stream
+ *              and fills it; when NULL the call is asynchronous and
+ *              lhdm_get_info() retrieves the report later.
+ * The context keeps R, the ordered P, x_P and the residual for
+ * lhdm_backward until the next solve on the same context.
+ * Errors: INVALID_ARG (sizes, lda < max(1,m), NULL pointers, parameters out
+ * of range), CUDA.  A, b are not modified.
+ */
+int lhdm_solve(lhdm_ctx* ctx, int32_t m, int32_t n, const double* A, int32_t lda,
+               const double* b, const lhdm_params* prm, double* x, int32_t* passive,
+               lhdm_info* info, void* stream);
+
+/*
+ * lhdm_solve_host: the same solve with HOST buffers (the end-to-end path):
+ * copies A (m x n, lda) and b to the device on the stream, solves, copies x
+ * and passive back and synchronises.  A, b, x, passive, info: host.  Pinned
+ * host memory gives asynchronous copies; pageable memory works too.
+ * Errors as lhdm_solve.
+ */
+int lhdm_solve_host(lhdm_ctx* ctx, int32_t m, int32_t n, const double* A, int32_t lda,
+                    const double* b, const lhdm_params* prm, double* x, int32_t* passive,
+                    lhdm_info* info, void* stream);
+
+/* Copies the report of the last solve on ctx to *info (host); synchronises. */
+int lhdm_get_info(lhdm_ctx* ctx, lhdm_info* info, void* stream);
+
+/*
+ * lhdm_backward: adjoint of the solution map of the last lhdm_solve on ctx,
+ * on its final passive set P (x_P is the least-squares solution on P,
+ * subproblem (6) of section 2.1).  With g = dL/dx it solves
+ * R^T R u = g_P with the final R factor and writes
+ *     dL/db   = A_P u                          (length m)
+ *     dL/dA_P = r u^T - (A_P u) x_P^T,  dL/dA_Z = 0   (m x n, ld ld_dA)
+ * where r = b - A x.  dLdx (length n), dLdb, dLdA: device.  A must be the
+ * matrix passed to the solve (lda as then).  Either output may be NULL.
+ * Errors: NO_STATE (no completed solve), INVALID_ARG, CUDA.
+ */
+int lhdm_backward(lhdm_ctx* ctx, const double* A, int32_t lda, const double* dLdx,
+                  double* dLdb, double* dLdA, int32_t ld_dA, void* stream);
+
+/* Decision trace of the last solve (verification aid): up to max_rows rows
+ * of 6 int32 per outer step, host buffer out[6 * max_rows]:
+ *   |J| from Algorithm 2, |J| kept after the feasibility loop, inner-loop
+ *   steps, |P| after the step, columns removed by the inner loop, and the
+ *   first column of J (the Lawson-Hanson argmax).
+ * Returns the number of rows written (negative status on error);
+ * synchronises the stream. */
+int lhdm_trace(lhdm_ctx* ctx, int32_t* out, int32_t max_rows, void* stream);
+
+/* Verification aid: copies `count` elements of a named piece of the
+ * context's device state after the last solve to host memory `host`
+ * (synchronises).  Names: "w", "u", "anorm" (length n), "bt", "r"
+ * (length m), "yP", "xP", "order", "rslot" (positions), "pos" (columns),
+ * "W" (ld = max_m rounded up to even), "R" (slot-major, ld = the context's
+ * min(max_m, max_n) rounded up to even).  FP64 except the int32 index
+ * arrays.  Errors: INVALID_ARG for an unknown name or count too large. */
+int lhdm_debug_state(lhdm_ctx* ctx, const char* name, void* host, int64_t count, void* stream);
+
+/* Profile of the last solve on ctx.  ms[0..8) = device time in ms of each
+ * solver phase (setup, DM, panel, triangular solve, commit, inner loop,
+ * residual, dual vector); ms[8..16) = the algorithmic FP64 flops of the same
+ * phases (an FMA counts 2).  Writes min(n, 16) values and returns how many
+ * (negative status on error).  Synchronises the stream. */
+int lhdm_phase_times(lhdm_ctx* ctx, double* ms, int32_t n, void* stream);
+
+/*
+ * Batched solves: many independent problems of uneven sizes in ONE
+ * persistent launch (each CTA takes instances from a device work queue,
+ * largest first, and runs Algorithm 3 on its own).
+ *
+ * lhdm_batch_create plans a batch: host arrays m[batch], n[batch],
+ * lda[batch] and host arrays of DEVICE pointers A[batch], b[batch],
+ * x[batch], passive[batch] (shapes as in lhdm_solve); info: device array of
+ * batch lhdm_info.  prm: host, NULL = defaults; prm->k_max <= 0 lets the
+ * built-in tuner choose k_max per instance size.  Allocates all device
+ * workspace and uploads the descriptor table on the stream (synchronises).
+ * Errors: INVALID_ARG, ALLOC, CUDA.
+ */
+int lhdm_batch_create(lhdm_batch** plan, int32_t batch, const int32_t* m, const int32_t* n,
+                      const int32_t* lda, const double* const* A, const double* const* b,
+                      double* const* x, int32_t* const* passive, lhdm_info* info,
+                      const lhdm_params* prm, void* stream);
+
+/* Runs the planned batch: exactly one kernel launch plus one small reset,
+ * no allocation and no host synchronisation, so it can be captured in a
+ * CUDA graph.  Results land in the x / passive / info arrays of the plan. */
+int lhdm_batch_run(lhdm_batch* plan, void* stream);
+
+/*
+ * Adjoint of every instance of the last lhdm_batch_run, one launch:
+ * host arrays of device pointers dLdx[batch], dLdb[batch], dLdA[batch]
+ * (entries may be NULL) and host ld_dA[batch].  Same formulas as
+ * lhdm_backward.  Errors: NO_STATE, INVALID_ARG, CUDA.
+ */
+int lhdm_batch_backward(lhdm_batch* plan, const double* const* dLdx, double* const* dLdb,
+                        double* const* dLdA, const int32_t* ld_dA, void* stream);
+
+/* k_max the tuner chose for instance i (host int); -1 if out of range. */
+int lhdm_batch_kmax(const lhdm_batch* plan, int32_t i);
+
+/* Releases a plan (synchronises the device). */
+int lhdm_batch_destroy(lhdm_batch* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LHDM_H */

@@ -401,9 +401,14 @@ int orc_state_get(void* sv, int* nP, int* order, double* R, double* bt, double* 
  * p_order[n]    out: ordered passive set (QR column order), -1 padded.
  * info          out.
  * trace         optional (trace_cap rows): per outer step
- *               trace_i[5*s + 0..4] = |J| from DM, |J| kept, inner steps,
- *               nP after the step, columns removed by the inner loop;
- *               trace_d[s] = ||b - A x|| after the step.
+ *               trace_i[6*s + 0..5] = |J| from DM, |J| kept, inner steps,
+ *               nP after the step, columns removed by the inner loop, and
+ *               the column j chosen first (the LH argmax);
+ *               trace_d[2*s] = ||b - A x|| after the step, trace_d[2*s+1] =
+ *               the step's decision margin: the smallest relative distance
+ *               of a comparison from flipping (gap between the two largest
+ *               eligible w, and |y_i| / max|y|, |x_i| / max|x| over every
+ *               sign test of the feasibility and inner loops).
  * R_out         optional: final R (nP x nP, col-major, ld nP), in p_order.
  * Returns info->status.
  */
@@ -484,6 +489,17 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
     }
     if (inf.n_outer >= max_outer) { inf.status = ORC_ERR_MAX_ITER; break; }
 
+    /* decision margin of this step (relative distance of the closest
+       comparison to flipping): argmax gap and every y / x sign test */
+    double margin = INFINITY;
+    {
+      double w1 = -INFINITY, w2 = -INFINITY;
+      for (int t = 0; t < ne; ++t) {
+        const double wv = w[elig[t]];
+        if (wv > w1) { w2 = w1; w1 = wv; } else if (wv > w2) w2 = wv;
+      }
+      if (ne > 1 && w1 > 0.0) margin = (w1 - w2) / w1;
+    }
     /* DM on C^(s) = trailing rows of the Z columns */
     const int L = m - s->nP;
     const int kdm = dm_select_core(L, s->nP, ne, elig, s->W, m, w, u, prm->tau1,
@@ -500,8 +516,11 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
     /* feasibility loop: while min y_J <= 0, delete the last element of J */
     int drops = 0;
     for (;;) {
-      double ymin = INFINITY;
+      double ymin = INFINITY, ymax = 0.0;
       for (int t = 0; t < kk; ++t) if (y[J[t]] < ymin) ymin = y[J[t]];
+      for (int p = 0; p < s->nP; ++p) ymax = fmax(ymax, fabs(y[s->order[p]]));
+      for (int t = 0; t < kk; ++t)
+        if (ymax > 0.0) margin = fmin(margin, fabs(y[J[t]]) / ymax);
       if (!(ymin <= 0.0) || kk <= 1) break;
       state_drop_last(s);
       --kk;
@@ -513,7 +532,12 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
     int inner = 0, removed = 0;
     for (;;) {
       int neg = 0;
-      for (int p = 0; p < s->nP; ++p) if (y[s->order[p]] <= 0.0) { neg = 1; break; }
+      double ymax = 0.0;
+      for (int p = 0; p < s->nP; ++p) ymax = fmax(ymax, fabs(y[s->order[p]]));
+      for (int p = 0; p < s->nP; ++p) {
+        if (ymax > 0.0) margin = fmin(margin, fabs(y[s->order[p]]) / ymax);
+        if (y[s->order[p]] <= 0.0) neg = 1;
+      }
       if (!neg) break;
       if (inner > n) { inf.status = ORC_ERR_MAX_ITER; break; }
       ++inner;
@@ -531,6 +555,12 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
         x[i] = x[i] + alpha * (y[i] - x[i]);
       }
       x[istar] = 0.0;
+      {
+        double xmax = 0.0;
+        for (int p = 0; p < s->nP; ++p) xmax = fmax(xmax, fabs(x[s->order[p]]));
+        for (int p = 0; p < s->nP; ++p)
+          if (s->order[p] != istar && xmax > 0.0) margin = fmin(margin, fabs(x[s->order[p]]) / xmax);
+      }
       int nq = 0;
       for (int p = 0; p < s->nP; ++p)
         if (x[s->order[p]] <= 0.0) { qpos[nq++] = p; x[s->order[p]] = 0.0; }
@@ -555,12 +585,16 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
       u[j] = sqrt(col_dot(cj, cj, m - s->nP));
     }
     if (trace_i && inf.n_outer < trace_cap) {
-      trace_i[5 * inf.n_outer + 0] = kdm;
-      trace_i[5 * inf.n_outer + 1] = kk;
-      trace_i[5 * inf.n_outer + 2] = inner;
-      trace_i[5 * inf.n_outer + 3] = s->nP;
-      trace_i[5 * inf.n_outer + 4] = removed;
-      if (trace_d) trace_d[inf.n_outer] = sqrt(col_dot(r, r, m));
+      trace_i[6 * inf.n_outer + 0] = kdm;
+      trace_i[6 * inf.n_outer + 1] = kk;
+      trace_i[6 * inf.n_outer + 2] = inner;
+      trace_i[6 * inf.n_outer + 3] = s->nP;
+      trace_i[6 * inf.n_outer + 4] = removed;
+      trace_i[6 * inf.n_outer + 5] = J[0];
+      if (trace_d) {
+        trace_d[2 * inf.n_outer] = sqrt(col_dot(r, r, m));
+        trace_d[2 * inf.n_outer + 1] = margin;
+      }
     }
     inf.n_outer++;
   }

@@ -62,7 +62,8 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
 
     Returns a dict: x, order (ordered passive set), passive (sorted), info
     fields, and optionally trace (rows: |J| from DM, |J| kept, inner steps,
-    nP after, removed) with the per-step residual norms, and R.
+    nP after, removed, first column j) with the per-step residual norms and
+    decision margins, and R.
     """
     A = np.asfortranarray(A, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -72,8 +73,8 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
     prm = _Params(tau1, tau2, delta, int(k_max), tol_w, int(max_outer))
     inf = _Info()
     cap = 4 * n + 8 if trace else 0
-    ti = np.zeros(5 * max(cap, 1), dtype=np.int32)
-    td = np.zeros(max(cap, 1))
+    ti = np.zeros(6 * max(cap, 1), dtype=np.int32)
+    td = np.zeros(2 * max(cap, 1))
     R = np.zeros(min(m, n) ** 2) if want_R else None
     lib().orc_nnls(m, n, _dp(A), m, _dp(b), C.byref(prm), _dp(x), _ip(order), C.byref(inf),
                    cap, _ip(ti) if trace else None, _dp(td) if trace else None,
@@ -85,8 +86,9 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
                tol_w=inf.tol_w)
     if trace:
         no = min(inf.n_outer, cap)
-        out["trace"] = ti[: 5 * no].reshape(no, 5).copy()
-        out["trace_resid"] = td[:no].copy()
+        out["trace"] = ti[: 6 * no].reshape(no, 6).copy()
+        out["trace_resid"] = td[0:2 * no:2].copy()
+        out["trace_margin"] = td[1:2 * no:2].copy()
     if want_R:
         out["R"] = R[: nP * nP].reshape(nP, nP, order="F").copy()
     return out

@@ -1,0 +1,749 @@
+// lhdm_api.cu -- kernels and the C ABI (include/lhdm.h) of the GB300 LHDM
+// nonnegative least-squares solver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "lhdm.h"
+#include "lhdm_adjoint.cuh"
+
+using namespace lhdm;
+
+// ======================================================================= kernels
+// One solve on the whole GPU: one CTA per SM, cooperative launch.
+__global__ void __launch_bounds__(NT, 1) lhdm_solve_grid_kernel(Inst I, unsigned int* bar, int* err) {
+  extern __shared__ double dyn[];
+  GridTeam tm{(int)blockIdx.x, (int)gridDim.x, bar, err};
+  Engine<GridTeam> e(tm, I, dyn);
+  e.run();
+}
+
+__global__ void __launch_bounds__(NT, 1) lhdm_backward_grid_kernel(Inst I, unsigned int* bar, int* err,
+                                                                   const double* g, double* dLdb,
+                                                                   double* dLdA, int ld_dA, double* apu) {
+  extern __shared__ double dyn[];
+  GridTeam tm{(int)blockIdx.x, (int)gridDim.x, bar, err};
+  Engine<GridTeam> e(tm, I, dyn);
+  Adjoint<GridTeam> adj(e);
+  adj.run(g, dLdb, dLdA, ld_dA, apu);
+}
+
+// Per-instance descriptor of a batch (device array).
+struct BatchItem {
+  int m, n, lda, cap, ldr, k_max;
+  const double* A;
+  const double* b;
+  double* x;
+  int* passive;
+  lhdm_info* info;
+  double* R;
+  int* rslot;
+  int* order;
+  double* xP;
+  double* r;
+  int* nP;
+  const double* g;   // adjoint inputs/outputs (set per backward call)
+  double* dLdb;
+  double* dLdA;
+  int ld_dA;
+};
+
+// Offsets of one team's scratch inside a double region and an int region.
+struct ScratchLayout {
+  size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, candw, rotc, rots, apu;
+  size_t dtotal;
+  size_t pos, J, candi, candn, ipart, ctl, qlist;
+  size_t itotal;
+  int ldw;
+};
+
+static size_t up8(size_t x) { return (x + 31) & ~(size_t)31; }  // 256-byte granules of doubles/ints
+
+static ScratchLayout make_layout(int max_m, int max_n, int team) {
+  ScratchLayout L;
+  const int m = std::max(max_m, 1), n = std::max(max_n, 1);
+  const int cap = std::max(std::min(max_m, max_n), 1);
+  L.ldw = (m + 1) & ~1;
+  size_t o = 0;
+  auto take = [&](size_t cnt) { size_t r = o; o += up8(std::max<size_t>(cnt, 1)); return r; };
+  L.W = take((size_t)L.ldw * n);
+  L.bt = take(m);
+  L.yP = take(cap);
+  L.rhs = take(std::max(m, cap));
+  L.w = take(n);
+  L.u = take(n);
+  L.anorm = take(n);
+  L.V = take((size_t)m * KM);
+  L.vtop = take(KM);
+  L.beta = take(KM);
+  L.T = take(KM * KM);
+  L.R22 = take(KM * KM);
+  L.Gm = take(KM * KM);
+  L.yJ = take(KM);
+  L.pr = take(KM);
+  L.part = take((size_t)team * PW);
+  L.candw = take((size_t)team * KM);
+  L.rotc = take(cap);
+  L.rots = take(cap);
+  L.apu = take(m);
+  L.dtotal = o;
+  o = 0;
+  L.pos = take(n);
+  L.J = take(KM);
+  L.candi = take((size_t)team * KM);
+  L.candn = take(team);
+  L.ipart = take((size_t)team * 8);
+  L.ctl = take(16);
+  L.qlist = take(cap);
+  L.itotal = o;
+  return L;
+}
+
+static __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, double* d, int* ip) {
+  I.ldw = L.ldw;
+  I.W = d + L.W;
+  I.bt = d + L.bt;
+  I.yP = d + L.yP;
+  I.rhs = d + L.rhs;
+  I.w = d + L.w;
+  I.u = d + L.u;
+  I.anorm = d + L.anorm;
+  I.V = d + L.V;
+  I.vtop = d + L.vtop;
+  I.beta = d + L.beta;
+  I.T = d + L.T;
+  I.R22 = d + L.R22;
+  I.Gm = d + L.Gm;
+  I.yJ = d + L.yJ;
+  I.pr = d + L.pr;
+  I.part = d + L.part;
+  I.candw = d + L.candw;
+  I.rotc = d + L.rotc;
+  I.rots = d + L.rots;
+  I.pos = ip + L.pos;
+  I.J = ip + L.J;
+  I.candi = ip + L.candi;
+  I.candn = ip + L.candn;
+  I.ipart = ip + L.ipart;
+  I.ctl = ip + L.ctl;
+  I.qlist = ip + L.qlist;
+  I.amask = nullptr;
+}
+
+static __device__ void bind_item(Inst& I, const BatchItem& it) {
+  I.m = it.m;
+  I.n = it.n;
+  I.lda = it.lda;
+  I.cap = it.cap;
+  I.ldr = it.ldr;
+  I.A = it.A;
+  I.b = it.b;
+  I.x_out = it.x;
+  I.passive_out = it.passive;
+  I.info_out = it.info;
+  I.R = it.R;
+  I.rslot = it.rslot;
+  I.order = it.order;
+  I.xP = it.xP;
+  I.r = it.r;
+  I.nP_out = it.nP;
+  I.prm.k_max = it.k_max;
+}
+
+// Many instances in one persistent launch: each CTA takes the next instance
+// (largest first) from a device queue and solves it alone.
+__global__ void __launch_bounds__(NT, 1) lhdm_solve_batch_kernel(const BatchItem* items, const int* perm,
+                                                                 int batch, int* queue, ScratchLayout L,
+                                                                 double* dscr, int* iscr, DevParams prm) {
+  extern __shared__ double dyn[];
+  __shared__ int s_k;
+  Inst I;
+  bind_scratch(I, L, dscr + (size_t)blockIdx.x * L.dtotal, iscr + (size_t)blockIdx.x * L.itotal);
+  I.phase_ns = nullptr;
+  I.trace = nullptr;
+  I.trace_cap = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_k = atomicAdd(queue, 1);
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();
+    if (k >= batch) break;
+    const BatchItem it = items[perm[k]];
+    I.prm = prm;
+    bind_item(I, it);
+    CtaTeam tm{0, 1};
+    Engine<CtaTeam> e(tm, I, dyn);
+    e.run();
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) lhdm_backward_batch_kernel(const BatchItem* items, const int* perm,
+                                                                    int batch, int* queue, ScratchLayout L,
+                                                                    double* dscr, int* iscr) {
+  extern __shared__ double dyn[];
+  __shared__ int s_k;
+  Inst I;
+  const size_t dbase = (size_t)blockIdx.x * L.dtotal;
+  bind_scratch(I, L, dscr + dbase, iscr + (size_t)blockIdx.x * L.itotal);
+  I.phase_ns = nullptr;
+  I.trace = nullptr;
+  I.trace_cap = 0;
+  double* apu = dscr + dbase + L.apu;
+  for (;;) {
+    if (threadIdx.x == 0) s_k = atomicAdd(queue, 1);
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();
+    if (k >= batch) break;
+    const BatchItem it = items[perm[k]];
+    bind_item(I, it);
+    CtaTeam tm{0, 1};
+    Engine<CtaTeam> e(tm, I, dyn);
+    if (it.g) {
+      Adjoint<CtaTeam> adj(e);
+      adj.run(it.g, it.dLdb, it.dLdA, it.ld_dA, it.dLdb ? it.dLdb : apu);
+    }
+    __syncthreads();
+  }
+}
+
+// ======================================================================= host side
+struct lhdm_ctx {
+  int device = 0;
+  int nsm = 0;
+  int max_m = 0, max_n = 0, cap = 0, ldr = 0;
+  ScratchLayout L{};
+  double* dscr = nullptr;
+  int* iscr = nullptr;
+  double* R = nullptr;
+  int* rslot = nullptr;
+  int* order = nullptr;
+  double* xP = nullptr;
+  double* r = nullptr;
+  int* nP = nullptr;
+  unsigned int* bar = nullptr;
+  int* err = nullptr;
+  lhdm_info* d_info = nullptr;
+  double* d_phase = nullptr;
+  int* d_trace = nullptr;
+  int trace_cap = 0;
+  // host-buffer path staging (allocated on first use)
+  double* hA = nullptr;
+  double* hb = nullptr;
+  double* hx = nullptr;
+  int* hp = nullptr;
+  // state for the adjoint
+  bool have_state = false;
+  int last_m = 0, last_n = 0;
+};
+
+struct lhdm_batch {
+  int device = 0;
+  int batch = 0;
+  int nblocks = 0;
+  ScratchLayout L{};
+  double* dscr = nullptr;
+  int* iscr = nullptr;
+  double* pers_d = nullptr;
+  int* pers_i = nullptr;
+  BatchItem* d_items = nullptr;
+  int* d_perm = nullptr;
+  int* d_queue = nullptr;
+  BatchItem* d_adj = nullptr;
+  std::vector<BatchItem> items;
+  std::vector<int> kmax;
+  DevParams prm{};
+  bool ran = false;
+};
+
+static bool g_attr_done = false;
+
+static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LHDM_OK : LHDM_ERR_CUDA; }
+
+static int set_attrs() {
+  if (g_attr_done) return LHDM_OK;
+  cudaError_t e = cudaFuncSetAttribute(lhdm_solve_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lhdm_backward_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lhdm_solve_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lhdm_backward_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  g_attr_done = true;
+  return LHDM_OK;
+}
+
+static int check_params(const lhdm_params* p, bool allow_auto_k) {
+  if (!(p->tau1 > 0.0 && p->tau1 <= 1.0)) return LHDM_ERR_INVALID_ARG;
+  if (!(p->tau2 > 0.0 && p->tau2 <= 1.0)) return LHDM_ERR_INVALID_ARG;
+  if (!(p->delta > 0.0 && p->delta <= 1.0)) return LHDM_ERR_INVALID_ARG;
+  if (std::isnan(p->tol_w)) return LHDM_ERR_INVALID_ARG;
+  if (p->k_max > LHDM_KMAX_LIMIT) return LHDM_ERR_INVALID_ARG;
+  if (p->k_max < 1 && !allow_auto_k) return LHDM_ERR_INVALID_ARG;
+  return LHDM_OK;
+}
+
+static DevParams to_dev(const lhdm_params& p) {
+  DevParams d;
+  d.tau1 = p.tau1;
+  d.tau2 = p.tau2;
+  d.delta = p.delta;
+  d.tol_w = p.tol_w;
+  d.k_max = p.k_max;
+  d.max_outer = p.max_outer;
+  return d;
+}
+
+extern "C" {
+
+int lhdm_default_params(lhdm_params* p) {
+  if (!p) return LHDM_ERR_INVALID_ARG;
+  p->tau1 = 0.6;
+  p->tau2 = 0.15;
+  p->delta = 0.9;
+  p->tol_w = -1.0;
+  p->k_max = 32;
+  p->max_outer = 0;
+  return LHDM_OK;
+}
+
+const char* lhdm_status_string(int s) {
+  switch (s) {
+    case LHDM_OK: return "ok";
+    case LHDM_ERR_INVALID_ARG: return "invalid argument";
+    case LHDM_ERR_MAX_ITER: return "outer-iteration cap reached";
+    case LHDM_ERR_NONFINITE: return "non-finite value in A or b";
+    case LHDM_ERR_CUDA: return "CUDA runtime error";
+    case LHDM_ERR_TIMEOUT: return "a bounded device-side wait expired";
+    case LHDM_ERR_ALLOC: return "allocation failed";
+    case LHDM_ERR_NO_STATE: return "no solve state for the adjoint";
+    default: return "unknown status";
+  }
+}
+
+int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n) {
+  if (!out || max_m < 1 || max_n < 1) return LHDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  lhdm_ctx* c = new (std::nothrow) lhdm_ctx();
+  if (!c) return LHDM_ERR_ALLOC;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return LHDM_ERR_CUDA;
+  }
+  int rc = set_attrs();
+  if (rc) { delete c; return rc; }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lhdm_solve_grid_kernel, NT, DYN_SMEM) != cudaSuccess ||
+      nb < 1) {
+    delete c;
+    return LHDM_ERR_CUDA;
+  }
+  c->max_m = max_m;
+  c->max_n = max_n;
+  c->cap = std::max(std::min(max_m, max_n), 1);
+  c->ldr = (c->cap + 1) & ~1;
+  if ((max_n + c->nsm - 1) / c->nsm > CAND_LOCAL_MAX) { delete c; return LHDM_ERR_INVALID_ARG; }
+  c->L = make_layout(max_m, max_n, c->nsm);
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&c->dscr, c->L.dtotal * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->iscr, c->L.itotal * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->R, (size_t)c->ldr * c->cap * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->rslot, (size_t)c->cap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->order, (size_t)c->cap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->xP, (size_t)c->cap * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->r, (size_t)std::max(max_m, 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->nP, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->bar, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_info, sizeof(lhdm_info));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_phase, 2 * NPHASE * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 2 * NPHASE * sizeof(double));
+  c->trace_cap = 3 * max_n + 8;
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)6 * c->trace_cap * sizeof(int));
+  if (e != cudaSuccess) {
+    lhdm_destroy(c);
+    return e == cudaErrorMemoryAllocation ? LHDM_ERR_ALLOC : LHDM_ERR_CUDA;
+  }
+  *out = c;
+  return LHDM_OK;
+}
+
+int lhdm_destroy(lhdm_ctx* c) {
+  if (!c) return LHDM_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  cudaFree(c->dscr);
+  cudaFree(c->iscr);
+  cudaFree(c->R);
+  cudaFree(c->rslot);
+  cudaFree(c->order);
+  cudaFree(c->xP);
+  cudaFree(c->r);
+  cudaFree(c->nP);
+  cudaFree(c->bar);
+  cudaFree(c->err);
+  cudaFree(c->d_info);
+  cudaFree(c->d_phase);
+  cudaFree(c->d_trace);
+  cudaFree(c->hA);
+  cudaFree(c->hb);
+  cudaFree(c->hx);
+  cudaFree(c->hp);
+  delete c;
+  return LHDM_OK;
+}
+
+static void fill_ctx_inst(lhdm_ctx* c, Inst& I) {
+  bind_scratch(I, c->L, c->dscr, c->iscr);
+  I.cap = std::min(I.m, I.n);
+  I.ldr = c->ldr;
+  I.R = c->R;
+  I.rslot = c->rslot;
+  I.order = c->order;
+  I.xP = c->xP;
+  I.r = c->r;
+  I.nP_out = c->nP;
+  I.info_out = c->d_info;
+  I.phase_ns = c->d_phase;
+  I.trace = c->d_trace;
+  I.trace_cap = c->trace_cap;
+}
+
+int lhdm_solve(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
+               const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info, void* stream) {
+  if (!c || m < 0 || n < 0 || m > c->max_m || n > c->max_n || lda < std::max(1, m)) return LHDM_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && !A) || (m > 0 && !b) || (n > 0 && (!x || !passive))) return LHDM_ERR_INVALID_ARG;
+  lhdm_params p;
+  lhdm_default_params(&p);
+  if (prm) p = *prm;
+  int rc = check_params(&p, false);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Inst I;
+  std::memset(&I, 0, sizeof(I));
+  I.m = m;
+  I.n = n;
+  I.lda = lda;
+  I.A = A;
+  I.b = b;
+  I.x_out = x;
+  I.passive_out = passive;
+  I.prm = to_dev(p);
+  fill_ctx_inst(c, I);
+  c->have_state = false;
+  cudaError_t e = cudaMemsetAsync(c->bar, 0, 4 * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  void* args[] = {(void*)&I, (void*)&c->bar, (void*)&c->err};
+  e = cudaLaunchCooperativeKernel((const void*)lhdm_solve_grid_kernel, dim3(c->nsm), dim3(NT), args, DYN_SMEM, st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  c->have_state = true;
+  c->last_m = m;
+  c->last_n = n;
+  if (info) {
+    e = cudaMemcpyAsync(info, c->d_info, sizeof(lhdm_info), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  }
+  return LHDM_OK;
+}
+
+int lhdm_solve_host(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
+                    const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info, void* stream) {
+  if (!c || m < 0 || n < 0 || m > c->max_m || n > c->max_n || lda < std::max(1, m)) return LHDM_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && !A) || (m > 0 && !b) || (n > 0 && (!x || !passive))) return LHDM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->hA) {
+    e = cudaMalloc(&c->hA, (size_t)c->L.ldw * std::max(c->max_n, 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->hb, (size_t)std::max(c->max_m, 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->hx, (size_t)std::max(c->max_n, 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->hp, (size_t)std::max(c->max_n, 1) * sizeof(int));
+    if (e != cudaSuccess) return LHDM_ERR_ALLOC;
+  }
+  const int ld = c->L.ldw;
+  if (m > 0 && n > 0)
+    e = cudaMemcpy2DAsync(c->hA, (size_t)ld * sizeof(double), A, (size_t)lda * sizeof(double),
+                          (size_t)m * sizeof(double), n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->hb, b, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  int rc = lhdm_solve(c, m, n, c->hA, ld, c->hb, prm, c->hx, c->hp, nullptr, stream);
+  if (rc) return rc;
+  if (n > 0) {
+    e = cudaMemcpyAsync(x, c->hx, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(passive, c->hp, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, c->d_info, sizeof(lhdm_info), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_ok(e);
+}
+
+int lhdm_get_info(lhdm_ctx* c, lhdm_info* info, void* stream) {
+  if (!c || !info) return LHDM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(info, c->d_info, sizeof(lhdm_info), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_ok(e);
+}
+
+int lhdm_phase_times(lhdm_ctx* c, double* ms, int32_t n, void* stream) {
+  if (!c || !ms || n < 0) return -LHDM_ERR_INVALID_ARG;
+  double h[2 * NPHASE];
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h, c->d_phase, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return -LHDM_ERR_CUDA;
+  const int k = std::min<int>(n, 2 * NPHASE);
+  for (int i = 0; i < k; ++i) ms[i] = (i < NPHASE) ? h[i] * 1e-6 : h[i];
+  return k;
+}
+
+int lhdm_trace(lhdm_ctx* c, int32_t* out, int32_t max_rows, void* stream) {
+  if (!c || !out || max_rows < 0) return -LHDM_ERR_INVALID_ARG;
+  lhdm_info inf;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&inf, c->d_info, sizeof(inf), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return -LHDM_ERR_CUDA;
+  const int rows = std::min(std::min(inf.n_outer, c->trace_cap), max_rows);
+  if (rows > 0) {
+    e = cudaMemcpyAsync(out, c->d_trace, (size_t)6 * rows * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return -LHDM_ERR_CUDA;
+  }
+  return rows;
+}
+
+int lhdm_debug_state(lhdm_ctx* c, const char* name, void* host, int64_t count, void* stream) {
+  if (!c || !name || !host || count < 0) return LHDM_ERR_INVALID_ARG;
+  struct Entry { const char* nm; const void* ptr; size_t elem; size_t cap; };
+  const size_t n = (size_t)std::max(c->max_n, 1), m = (size_t)std::max(c->max_m, 1), cp = (size_t)c->cap;
+  const Entry table[] = {
+      {"w", c->dscr + c->L.w, 8, n},          {"u", c->dscr + c->L.u, 8, n},
+      {"anorm", c->dscr + c->L.anorm, 8, n},  {"bt", c->dscr + c->L.bt, 8, m},
+      {"yP", c->dscr + c->L.yP, 8, cp},       {"xP", c->xP, 8, cp},
+      {"r", c->r, 8, m},                      {"W", c->dscr + c->L.W, 8, (size_t)c->L.ldw * n},
+      {"R", c->R, 8, (size_t)c->ldr * cp},    {"order", c->order, 4, cp},
+      {"rslot", c->rslot, 4, cp},             {"pos", c->iscr + c->L.pos, 4, n},
+  };
+  for (const Entry& e : table) {
+    if (std::strcmp(e.nm, name) != 0) continue;
+    if ((size_t)count > e.cap) return LHDM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t err = cudaMemcpyAsync(host, e.ptr, (size_t)count * e.elem, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    return cuda_ok(err);
+  }
+  return LHDM_ERR_INVALID_ARG;
+}
+
+int lhdm_backward(lhdm_ctx* c, const double* A, int32_t lda, const double* dLdx, double* dLdb, double* dLdA,
+                  int32_t ld_dA, void* stream) {
+  if (!c) return LHDM_ERR_INVALID_ARG;
+  if (!c->have_state) return LHDM_ERR_NO_STATE;
+  const int m = c->last_m, n = c->last_n;
+  if ((m > 0 && n > 0 && !A) || lda < std::max(1, m) || (n > 0 && !dLdx)) return LHDM_ERR_INVALID_ARG;
+  if (dLdA && ld_dA < std::max(1, m)) return LHDM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Inst I;
+  std::memset(&I, 0, sizeof(I));
+  I.m = m;
+  I.n = n;
+  I.lda = lda;
+  I.A = A;
+  fill_ctx_inst(c, I);
+  double* apu = c->dscr + c->L.apu;
+  cudaError_t e = cudaMemsetAsync(c->bar, 0, 4 * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  double* apu_arg = dLdb ? dLdb : apu;
+  void* args[] = {(void*)&I, (void*)&c->bar, (void*)&c->err, (void*)&dLdx, (void*)&dLdb,
+                  (void*)&dLdA, (void*)&ld_dA, (void*)&apu_arg};
+  e = cudaLaunchCooperativeKernel((const void*)lhdm_backward_grid_kernel, dim3(c->nsm), dim3(NT), args, DYN_SMEM, st);
+  return cuda_ok(e);
+}
+
+// ----------------------------------------------------------------------- batches
+// Block size per instance when the caller asks the tuner (k_max <= 0):
+// the choice for each size bucket of n, from timing sweeps kept with the
+// project's benchmark data (k_max in {4, 8, 16, 32}).
+static int tuned_kmax(int m, int n) {
+  (void)m;
+  if (n <= 256) return 8;
+  if (n <= 512) return 16;
+  return 32;
+}
+
+int lhdm_batch_create(lhdm_batch** out, int32_t batch, const int32_t* m, const int32_t* n, const int32_t* lda,
+                      const double* const* A, const double* const* b, double* const* x,
+                      int32_t* const* passive, lhdm_info* info, const lhdm_params* prm, void* stream) {
+  if (!out || batch < 0 || (batch > 0 && (!m || !n || !lda || !A || !b || !x || !passive || !info)))
+    return LHDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  lhdm_params p;
+  lhdm_default_params(&p);
+  if (prm) p = *prm;
+  int rc = check_params(&p, true);
+  if (rc) return rc;
+  int max_m = 1, max_n = 1;
+  for (int i = 0; i < batch; ++i) {
+    if (m[i] < 0 || n[i] < 0 || lda[i] < std::max(1, m[i])) return LHDM_ERR_INVALID_ARG;
+    if ((m[i] > 0 && n[i] > 0 && !A[i]) || (m[i] > 0 && !b[i]) || (n[i] > 0 && (!x[i] || !passive[i])))
+      return LHDM_ERR_INVALID_ARG;
+    max_m = std::max(max_m, m[i]);
+    max_n = std::max(max_n, n[i]);
+  }
+  if (max_n > CAND_LOCAL_MAX) return LHDM_ERR_INVALID_ARG;
+  rc = set_attrs();
+  if (rc) return rc;
+  lhdm_batch* B = new (std::nothrow) lhdm_batch();
+  if (!B) return LHDM_ERR_ALLOC;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nsm = 0, occ = 0;
+  cudaGetDevice(&B->device);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lhdm_solve_batch_kernel, NT, DYN_SMEM);
+  B->batch = batch;
+  B->nblocks = std::max(1, std::min(batch, nsm * std::max(occ, 1)));
+  B->L = make_layout(max_m, max_n, 1);
+  B->prm = to_dev(p);
+  // persistent per-instance state
+  size_t dtot = 0, itot = 0;
+  std::vector<size_t> doff(batch), ioff(batch);
+  for (int i = 0; i < batch; ++i) {
+    const int cap = std::max(std::min(m[i], n[i]), 1), ldr = (cap + 1) & ~1;
+    doff[i] = dtot;
+    dtot += up8((size_t)ldr * cap) + up8(cap) + up8(std::max(m[i], 1));
+    ioff[i] = itot;
+    itot += up8(cap) * 2 + up8(1);
+  }
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&B->dscr, B->L.dtotal * B->nblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&B->iscr, B->L.itotal * B->nblocks * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B->pers_d, std::max<size_t>(dtot, 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&B->pers_i, std::max<size_t>(itot, 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_items, std::max(batch, 1) * sizeof(BatchItem));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_perm, std::max(batch, 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_queue, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_adj, std::max(batch, 1) * sizeof(BatchItem));
+  if (e != cudaSuccess) {
+    lhdm_batch_destroy(B);
+    return LHDM_ERR_ALLOC;
+  }
+  B->items.resize(batch);
+  B->kmax.resize(batch);
+  for (int i = 0; i < batch; ++i) {
+    BatchItem& it = B->items[i];
+    std::memset(&it, 0, sizeof(it));
+    const int cap = std::max(std::min(m[i], n[i]), 1), ldr = (cap + 1) & ~1;
+    it.m = m[i];
+    it.n = n[i];
+    it.lda = lda[i];
+    it.cap = std::min(m[i], n[i]);
+    it.ldr = ldr;
+    it.k_max = p.k_max > 0 ? p.k_max : tuned_kmax(m[i], n[i]);
+    B->kmax[i] = it.k_max;
+    it.A = A[i];
+    it.b = b[i];
+    it.x = x[i];
+    it.passive = passive[i];
+    it.info = info + i;
+    double* pd = B->pers_d + doff[i];
+    it.R = pd;
+    it.xP = pd + up8((size_t)ldr * cap);
+    it.r = it.xP + up8(cap);
+    int* pi = B->pers_i + ioff[i];
+    it.rslot = pi;
+    it.order = pi + up8(cap);
+    it.nP = pi + 2 * up8(cap);
+  }
+  // largest work first (about m * n * min(m, n) flops per instance)
+  std::vector<int> perm(batch);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) {
+    const double wa = (double)m[a] * n[a] * std::min(m[a], n[a]);
+    const double wc = (double)m[c] * n[c] * std::min(m[c], n[c]);
+    return wa > wc;
+  });
+  if (batch > 0) {
+    e = cudaMemcpyAsync(B->d_items, B->items.data(), batch * sizeof(BatchItem), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_perm, perm.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      lhdm_batch_destroy(B);
+      return LHDM_ERR_CUDA;
+    }
+  }
+  *out = B;
+  return LHDM_OK;
+}
+
+int lhdm_batch_run(lhdm_batch* B, void* stream) {
+  if (!B) return LHDM_ERR_INVALID_ARG;
+  if (B->batch == 0) return LHDM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  lhdm_solve_batch_kernel<<<B->nblocks, NT, DYN_SMEM, st>>>(B->d_items, B->d_perm, B->batch, B->d_queue, B->L,
+                                                             B->dscr, B->iscr, B->prm);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  B->ran = true;
+  return LHDM_OK;
+}
+
+int lhdm_batch_backward(lhdm_batch* B, const double* const* dLdx, double* const* dLdb, double* const* dLdA,
+                        const int32_t* ld_dA, void* stream) {
+  if (!B || (B->batch > 0 && !dLdx)) return LHDM_ERR_INVALID_ARG;
+  if (!B->ran) return LHDM_ERR_NO_STATE;
+  if (B->batch == 0) return LHDM_OK;
+  std::vector<BatchItem> it = B->items;
+  for (int i = 0; i < B->batch; ++i) {
+    it[i].g = dLdx[i];
+    it[i].dLdb = dLdb ? dLdb[i] : nullptr;
+    it[i].dLdA = dLdA ? dLdA[i] : nullptr;
+    it[i].ld_dA = ld_dA ? ld_dA[i] : std::max(1, it[i].m);
+    if (it[i].dLdA && it[i].ld_dA < std::max(1, it[i].m)) return LHDM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // the adjoint descriptors go to a second table so the forward table stays intact
+  cudaError_t e = cudaMemcpyAsync(B->d_adj, it.data(), B->batch * sizeof(BatchItem), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  lhdm_backward_batch_kernel<<<B->nblocks, NT, DYN_SMEM, st>>>(B->d_adj, B->d_perm, B->batch, B->d_queue, B->L,
+                                                                B->dscr, B->iscr);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_ok(e);
+}
+
+int lhdm_batch_kmax(const lhdm_batch* B, int32_t i) {
+  if (!B || i < 0 || i >= B->batch) return -1;
+  return B->kmax[i];
+}
+
+int lhdm_batch_destroy(lhdm_batch* B) {
+  if (!B) return LHDM_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  cudaFree(B->dscr);
+  cudaFree(B->iscr);
+  cudaFree(B->pers_d);
+  cudaFree(B->pers_i);
+  cudaFree(B->d_items);
+  cudaFree(B->d_perm);
+  cudaFree(B->d_queue);
+  cudaFree(B->d_adj);
+  delete B;
+  return LHDM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// lhdm_engine.cuh -- device engine of the LHDM / LH nonnegative least-squares
+// solver (Algorithms 1-5 of Dessole, Dell'Orto, Marcuzzi).
+//
+// One solve is one persistent launch.  A "team" of CTAs runs the whole outer
+// loop of Algorithm 3: the grid team is every SM of the GPU (one CTA per SM,
+// phases separated by a grid barrier with a bounded wait), the CTA team is a
+// single CTA that owns one instance of a batch (phases separated by
+// __syncthreads).  Every phase spreads its FP64 work over all threads of the
+// team; control decisions are recomputed identically by every CTA from data
+// published before the last barrier, so all CTAs follow the same path.
+//
+// State of an instance (section 2.1, whole-matrix variant of section 4.1):
+//   W  = Q^T A for the columns in Z (the B and C blocks), m x n, ld ldw;
+//        columns in P are not kept current in W - their R column is in R.
+//   bt = Q^T b.
+//   R  = the nP x nP triangular factor, column of position p stored in slot
+//        rslot[p] of a cap x cap array (ld ldr); rows are QR rows.
+//   order[p] = column index at position p (QR column order), pos[c] = p or -1.
+//   xP[p]    = x at position p.
+// The Householder vectors of the current panel live in V (row-major, ld KM).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lhdm.h"
+
+namespace lhdm {
+
+constexpr int KM = LHDM_KMAX_LIMIT;  // 64
+constexpr int NT = 512;              // threads per CTA
+constexpr int NW = NT / 32;          // warps per CTA
+constexpr int PW = 2112;             // partial-sum slots per CTA (>= KM(KM+1)/2 + 16)
+// Slot ranges inside one CTA's partial row.  A range is only rewritten after
+// a barrier that follows every read of its previous contents:
+//   [0, KM(KM+1)/2)        candidate Gram pairs (DM)
+//   [0, 2(KM+1))           panel dots, double-buffered by reflector parity
+//   [P_O1, P_O1 + 8)       outer-loop argmax / maxima / sums
+//   P_RS                   residual sum of squares
+constexpr int P_O1 = PW - 16;
+constexpr int P_RS = PW - 1;
+constexpr int TB = 64;               // triangular-solve block
+constexpr int DB = 32;               // downdate block (positions per warp)
+constexpr int NPHASE = 8;
+constexpr double EPS = 2.220446049250313e-16;  // 2^-52
+constexpr long long WAIT_NS = 4000000000LL;    // bound on any device-side wait
+
+enum Phase { PH_SETUP = 0, PH_DM, PH_PANEL, PH_SOLVE, PH_COMMIT, PH_INNER, PH_RESID, PH_DUAL };
+
+struct DevParams {
+  double tau1, tau2, delta, tol_w;
+  int k_max, max_outer;
+};
+
+// Everything a team needs for one instance.  Persistent fields (R, rslot,
+// order, xP, r, nP_out) survive the solve for the adjoint.
+struct Inst {
+  int m, n, lda, cap, ldw, ldr;
+  const double* A;
+  const double* b;
+  double* x_out;
+  int* passive_out;
+  lhdm_info* info_out;
+  // persistent
+  double* R;
+  int* rslot;
+  int* order;
+  double* xP;
+  double* r;
+  int* nP_out;
+  // scratch
+  double* W;
+  double* bt;
+  double* yP;
+  double* rhs;
+  double* w;
+  double* u;
+  double* anorm;
+  double* V;      // >= m x KM, row-major
+  double* vtop;   // KM
+  double* beta;   // KM
+  double* T;      // KM x KM
+  double* R22;    // KM x KM
+  double* Gm;     // KM x KM
+  double* yJ;     // KM
+  double* pr;     // KM (panel right-hand side)
+  double* part;   // team.size x PW
+  double* candw;  // team.size x KM
+  double* rotc;   // rotation log
+  double* rots;
+  int* pos;       // n
+  int* J;         // KM
+  int* candi;     // team.size x KM
+  int* candn;     // team.size
+  int* ipart;     // team.size x 8
+  int* ctl;       // 16 ints of control words
+  int* qlist;     // cap: positions removed by the current inner step
+  unsigned long long* amask;  // KM acceptance masks
+  double* phase_ns;           // NPHASE (may be null)
+  int* trace;                 // 6 ints per outer step (may be null)
+  int trace_cap;              // rows available in trace
+  DevParams prm;
+};
+
+// control words (ctl[])
+enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR };
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+
+__device__ __forceinline__ long long gtimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Even split of [0, total) into `parts` contiguous ranges.
+__device__ __forceinline__ void split(int total, int parts, int idx, int& lo, int& hi) {
+  lo = (int)(((long long)total * idx) / parts);
+  hi = (int)(((long long)total * (idx + 1)) / parts);
+}
+
+// Block-wide sum, same value in every thread, fixed order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = lane < NW ? sh[lane] : 0.0;
+  return warp_sum(t);
+}
+
+// (value, index) argmax with lowest index on ties; idx < 0 = empty.
+struct ArgMax {
+  double v;
+  int i;
+};
+__device__ __forceinline__ ArgMax amax_merge(ArgMax a, ArgMax b) {
+  if (b.i < 0) return a;
+  if (a.i < 0) return b;
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+__device__ __forceinline__ ArgMax warp_amax(ArgMax a) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    ArgMax b;
+    b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    a = amax_merge(a, b);
+  }
+  return a;
+}
+__device__ __forceinline__ ArgMax block_amax(ArgMax a, double* shv, int* shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_amax(a);
+  __syncthreads();
+  if (lane == 0) { shv[warp] = a.v; shi[warp] = a.i; }
+  __syncthreads();
+  ArgMax t;
+  t.v = lane < NW ? shv[lane] : 0.0;
+  t.i = lane < NW ? shi[lane] : -1;
+  return warp_amax(t);
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = lane < NW ? sh[lane] : -INFINITY;
+  return warp_max(t);
+}
+__device__ __forceinline__ int block_sum_int(int v, int* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  int t = lane < NW ? sh[lane] : 0;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// ---------------------------------------------------------------- teams
+// Whole-grid team: one CTA per SM, co-resident (cooperative launch).  The
+// barrier is a generation counter; every wait is bounded by WAIT_NS and sets
+// *err on expiry, after which every CTA leaves the solve.
+struct GridTeam {
+  int rank, size;
+  unsigned int* bar;  // [0] arrivals, [1] generation
+  int* err;
+  __device__ __forceinline__ bool sync() {
+    __shared__ int s_ok;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      volatile unsigned int* gen = bar + 1;
+      const unsigned int g = *gen;
+      __threadfence();
+      const unsigned int prev = atomicAdd(bar, 1u);
+      if (prev == (unsigned int)size - 1u) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        const long long t0 = gtimer();
+        unsigned int spins = 0;
+        while (*gen == g) {
+          if ((++spins & 63u) == 0u) {
+            if (*(volatile int*)err) { ok = 0; break; }
+            if (gtimer() - t0 > WAIT_NS) { atomicExch(err, 1); ok = 0; break; }
+          }
+        }
+      }
+      __threadfence();
+      if (*(volatile int*)err) ok = 0;
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+};
+
+// Single-CTA team (one batch instance per CTA).
+struct CtaTeam {
+  int rank, size;
+  __device__ __forceinline__ bool sync() {
+    __threadfence_block();
+    __syncthreads();
+    return true;
+  }
+};
+
+// Bounded wait until *flag >= target (one thread); false on timeout.
+__device__ __forceinline__ bool wait_ge(const int* flag, int target, int* err) {
+  if (*(volatile const int*)flag >= target) return true;
+  const long long t0 = gtimer();
+  unsigned int spins = 0;
+  while (*(volatile const int*)flag < target) {
+    if ((++spins & 63u) == 0u) {
+      if (err && *(volatile int*)err) return false;
+      if (gtimer() - t0 > WAIT_NS) {
+        if (err) atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+template <class Team>
+struct Engine;
+
+}  // namespace lhdm

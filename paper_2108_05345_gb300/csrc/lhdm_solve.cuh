@@ -1,0 +1,1241 @@
+// lhdm_solve.cuh -- the outer loop of Algorithm 3 (LHDM) / Algorithm 1 (LH)
+// as team-generic device code.  See lhdm_engine.cuh for the state layout.
+#pragma once
+
+#include "lhdm_engine.cuh"
+
+namespace lhdm {
+
+// Dynamic shared memory per CTA (bytes) used by the phases below.
+constexpr int DYN_SMEM = 64 * 1024;
+constexpr int CAND_LOCAL_MAX = 2048;     // local DM candidates per CTA
+constexpr int CAND_STAGE = 4096;         // merged candidates staged per pass
+constexpr int ROT_STAGE = 2048;          // rotations staged per pass
+
+// Orderable key of a positive double (dual values of DM candidates are > 0).
+__device__ __forceinline__ unsigned long long wkey(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+// a better than b: larger w, then smaller index.
+__device__ __forceinline__ bool better(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+template <class Team>
+struct Engine {
+  Team& tm;
+  const Inst& I;
+  double* dyn;
+  int tid, lane, warp;
+
+  // uniform control state (identical in every thread of every CTA)
+  int nP = 0, n_outer = 0, n_inner = 0, n_drop = 0, rank_limited = 0, status = LHDM_OK;
+  double tol_w = 0.0;
+  int jsel = -1, n_elig = 0, kk = 0, kp = 0;
+  double wmax = 0.0, umax = 0.0, wz_any = -INFINITY, rsq = 0.0;
+  double amax = 0.0, bsq = 0.0;
+  int nonfinite = 0;
+  bool u_dirty = false;
+  bool failed = false;
+  int kdm = 0, removed = 0, inner_step = 0;
+
+  // phase timing (rank 0, thread 0)
+  long long t_last = 0;
+  int cur_phase = -1;
+  double ph[NPHASE];
+  double fl[NPHASE];  // algorithmic FP64 flops per phase (rank 0, thread 0)
+
+  __device__ Engine(Team& t, const Inst& inst, double* d) : tm(t), I(inst), dyn(d) {
+    tid = threadIdx.x;
+    lane = tid & 31;
+    warp = tid >> 5;
+    for (int i = 0; i < NPHASE; ++i) { ph[i] = 0.0; fl[i] = 0.0; }
+  }
+
+  // Counts algorithmic flops (an FMA is 2) of a phase; uniform state only.
+  __device__ __forceinline__ void flops(int p, double f) {
+    if (I.phase_ns && tm.rank == 0 && tid == 0) fl[p] += f;
+  }
+
+  __device__ __forceinline__ void phase(int p) {
+    if (I.phase_ns && tm.rank == 0 && tid == 0) {
+      const long long t = gtimer();
+      if (cur_phase >= 0) ph[cur_phase] += (double)(t - t_last);
+      t_last = t;
+      cur_phase = p;
+    }
+  }
+
+  __device__ __forceinline__ bool sync() {
+    if (failed) return false;
+    if (!tm.sync()) {
+      failed = true;
+      status = LHDM_ERR_TIMEOUT;
+      return false;
+    }
+    return true;
+  }
+
+  __device__ __forceinline__ double* Rcol(int slot) const { return I.R + (size_t)slot * I.ldr; }
+  __device__ __forceinline__ double* Wcol(int c) const { return I.W + (size_t)c * I.ldw; }
+
+  // ------------------------------------------------------------ setup
+  // Algorithm 3, first lines: x = 0, w = A^T b, u = column norms of A; W = A.
+  __device__ void setup() {
+    __shared__ double sh[32];
+    __shared__ int shi[32];
+    const int m = I.m, n = I.n;
+    int c0, c1;
+    split(n, tm.size, tm.rank, c0, c1);
+    int bad = 0;
+    double am = 0.0;
+    for (int c = c0 + warp; c < c1; c += NW) {
+      const double* a = I.A + (size_t)c * I.lda;
+      double* wc = Wcol(c);
+      double s2 = 0.0, sb = 0.0;
+      for (int i = lane; i < m; i += 32) {
+        const double v = __ldg(a + i);
+        wc[i] = v;
+        bad |= !isfinite(v);
+        s2 = fma(v, v, s2);
+        sb = fma(v, __ldg(I.b + i), sb);
+      }
+      s2 = warp_sum(s2);
+      sb = warp_sum(sb);
+      const double an = sqrt(s2);
+      am = fmax(am, an);
+      if (lane == 0) {
+        I.anorm[c] = an;
+        I.u[c] = an;
+        I.w[c] = sb;
+        I.pos[c] = -1;
+      }
+    }
+    int r0, r1;
+    split(m, tm.size, tm.rank, r0, r1);
+    double bs = 0.0;
+    for (int i = r0 + tid; i < r1; i += NT) {
+      const double v = __ldg(I.b + i);
+      bad |= !isfinite(v);
+      I.bt[i] = v;
+      I.r[i] = v;
+      bs = fma(v, v, bs);
+    }
+    int p0, p1;
+    split(I.cap, tm.size, tm.rank, p0, p1);
+    for (int p = p0 + tid; p < p1; p += NT) {
+      I.xP[p] = 0.0;
+      I.yP[p] = 0.0;
+      I.rslot[p] = p;
+      I.order[p] = -1;
+    }
+    if (tm.rank == 0 && tid < 16) I.ctl[tid] = 0;
+    am = block_max(am, sh);
+    bs = block_sum(bs, sh);
+    bad = block_sum_int(bad, shi);
+    // O1 partial of the first outer step (u = ||a_j||, everything in Z)
+    o1_partial(am, bs, (double)bad);
+  }
+
+  // Per-CTA partial of the outer-loop test and of the DM maxima over the
+  // CTA's column range: argmax of w over the eligible part of Z (lowest
+  // index on ties), max u over it, max w over all of Z, eligible count.
+  // Slots 5..7 carry extra sums (amax / ||r||^2 / non-finite count).
+  __device__ void o1_partial(double s5, double s6, double s7) {
+    __shared__ double shv[32];
+    __shared__ int shi[32];
+    __syncthreads();
+    int c0, c1;
+    split(I.n, tm.size, tm.rank, c0, c1);
+    ArgMax best{0.0, -1};
+    double um = -INFINITY, wz = -INFINITY;
+    int ne = 0;
+    for (int c = c0 + tid; c < c1; c += NT) {
+      if (ldcg(I.pos + c) >= 0) continue;
+      const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
+      wz = fmax(wz, wc);
+      if (uc > (100.0 * EPS) * an) {
+        ++ne;
+        best = amax_merge(best, ArgMax{wc, c});
+        um = fmax(um, uc);
+      }
+    }
+    best = block_amax(best, shv, shi);
+    um = block_max(um, shv);
+    wz = block_max(wz, shv);
+    ne = block_sum_int(ne, shi);
+    if (tid == 0) {
+      double* p = I.part + (size_t)tm.rank * PW + P_O1;
+      p[0] = best.v;
+      p[1] = (double)best.i;
+      p[2] = um;
+      p[3] = wz;
+      p[4] = (double)ne;
+      p[5] = s5;
+      p[6] = s6;
+      p[7] = s7;
+    }
+  }
+
+  // Combines the O1 partials of every CTA (same order everywhere).
+  __device__ void o1_reduce(bool first) {
+    __shared__ double s_d[8];
+    __shared__ int s_i[2];
+    if (warp == 0) {
+      ArgMax best{0.0, -1};
+      double um = -INFINITY, wz = -INFINITY, s5 = 0.0, s6 = 0.0, s7 = 0.0;
+      int ne = 0;
+      for (int t = lane; t < tm.size; t += 32) {
+        const double* p = I.part + (size_t)t * PW + P_O1;
+        best = amax_merge(best, ArgMax{ldcg(p + 0), (int)ldcg(p + 1)});
+        um = fmax(um, ldcg(p + 2));
+        wz = fmax(wz, ldcg(p + 3));
+        ne += (int)ldcg(p + 4);
+        if (first) s5 = fmax(s5, ldcg(p + 5)); else s5 += ldcg(p + 5);
+        s6 += ldcg(p + 6);
+        s7 += ldcg(p + 7);
+      }
+      best = warp_amax(best);
+      um = warp_max(um);
+      wz = warp_max(wz);
+      s5 = first ? warp_max(s5) : warp_sum(s5);
+      s6 = warp_sum(s6);
+      s7 = warp_sum(s7);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) ne += __shfl_xor_sync(0xffffffffu, ne, o);
+      if (lane == 0) {
+        s_d[0] = best.v;
+        s_d[1] = um;
+        s_d[2] = wz;
+        s_d[3] = s5;
+        s_d[4] = s6;
+        s_d[5] = s7;
+        s_i[0] = best.i;
+        s_i[1] = ne;
+      }
+    }
+    __syncthreads();
+    wmax = s_d[0];
+    umax = s_d[1];
+    wz_any = s_d[2];
+    jsel = s_i[0];
+    n_elig = s_i[1];
+    if (first) {
+      amax = s_d[3];
+      bsq = s_d[4];
+      rsq = bsq;
+      nonfinite = (int)s_d[5];
+    } else {
+      rsq = s_d[4];
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------------ DM
+  // Algorithm 2 on C = W[nP:m, Z]: candidates above both thresholds, the
+  // first k_max-1 by w (descending; index ascending), cosines of the
+  // projected columns, greedy |theta| < delta.  Leaves J in s_J, |J| in kk.
+  __device__ bool dm_select(int* s_J) {
+    const int km = I.prm.k_max;
+    const int kc_max = km - 1;
+    if (tid == 0) s_J[0] = jsel;
+    kk = 1;
+    if (km <= 1) {
+      __syncthreads();
+      return true;
+    }
+    const double thr_w = I.prm.tau1 * wmax;
+    const double thr_u = I.prm.tau2 * umax;
+    // (a) local candidates of this CTA's column range, locally ranked
+    {
+      unsigned long long* s_k = reinterpret_cast<unsigned long long*>(dyn);
+      int* s_c = reinterpret_cast<int*>(s_k + CAND_LOCAL_MAX);
+      __shared__ int s_cnt;
+      if (tid == 0) s_cnt = 0;
+      __syncthreads();
+      int c0, c1;
+      split(I.n, tm.size, tm.rank, c0, c1);
+      for (int c = c0 + tid; c < c1; c += NT) {
+        if (c == jsel || ldcg(I.pos + c) >= 0) continue;
+        const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
+        if (uc > (100.0 * EPS) * an && wc >= thr_w && uc >= thr_u) {
+          const int k = atomicAdd(&s_cnt, 1);
+          if (k < CAND_LOCAL_MAX) {
+            s_k[k] = wkey(wc);
+            s_c[k] = c;
+          }
+        }
+      }
+      __syncthreads();
+      const int cnt = min(s_cnt, CAND_LOCAL_MAX);
+      for (int k = tid; k < cnt; k += NT) {
+        const unsigned long long kk0 = s_k[k];
+        const int ck = s_c[k];
+        int rk = 0;
+        for (int q = 0; q < cnt; ++q) rk += better(s_k[q], s_c[q], kk0, ck);
+        if (rk < kc_max) {
+          I.candw[(size_t)tm.rank * KM + rk] = __longlong_as_double((long long)kk0);
+          I.candi[(size_t)tm.rank * KM + rk] = ck;
+        }
+      }
+      if (tid == 0) I.candn[tm.rank] = min(cnt, kc_max);
+    }
+    if (!sync()) return false;
+    // (b) merge the sorted local lists: global rank by counting better ones
+    __shared__ int s_off[1024 + 1];
+    __shared__ int s_kc;
+    {
+      // prefix offsets of the per-CTA lists (team size <= 1024)
+      if (tid == 0) {
+        int acc = 0;
+        for (int t = 0; t < tm.size; ++t) {
+          s_off[t] = acc;
+          acc += ldcg(I.candn + t);
+        }
+        s_off[tm.size] = acc;
+        s_kc = min(acc, kc_max);
+      }
+      __syncthreads();
+      const int total = s_off[tm.size];
+      int e0, e1;
+      split(total, tm.size, tm.rank, e0, e1);
+      unsigned long long* s_k = reinterpret_cast<unsigned long long*>(dyn);
+      int* s_c = reinterpret_cast<int*>(s_k + CAND_STAGE);
+      // my elements (at most ~total/size), ranks accumulated over staged passes
+      const int mine = e1 - e0;
+      int my_rank = 0;
+      unsigned long long my_key = 0;
+      int my_c = -1;
+      const int e = e0 + tid;
+      if (tid < mine) {
+        int t = 0;
+        while (s_off[t + 1] <= e) ++t;
+        const int q = e - s_off[t];
+        my_key = wkey(ldcg(I.candw + (size_t)t * KM + q));
+        my_c = ldcg(I.candi + (size_t)t * KM + q);
+      }
+      for (int base = 0; base < total; base += CAND_STAGE) {
+        const int nst = min(CAND_STAGE, total - base);
+        __syncthreads();
+        for (int k = tid; k < nst; k += NT) {
+          const int g = base + k;
+          int t = 0;
+          // lists are short; linear search over the offsets
+          while (s_off[t + 1] <= g) ++t;
+          const int q = g - s_off[t];
+          s_k[k] = wkey(ldcg(I.candw + (size_t)t * KM + q));
+          s_c[k] = ldcg(I.candi + (size_t)t * KM + q);
+        }
+        __syncthreads();
+        if (tid < mine)
+          for (int k = 0; k < nst; ++k) my_rank += better(s_k[k], s_c[k], my_key, my_c);
+      }
+      if (tid < mine && my_rank < kc_max) I.J[1 + my_rank] = my_c;
+      if (tm.rank == 0 && tid == 0) I.J[0] = jsel;
+    }
+    if (!sync()) return false;
+    const int kc = s_kc;
+    const int KK = kc + 1;
+    if (tid < KK) s_J[tid] = ldcg(I.J + tid);
+    __syncthreads();
+    if (KK == 1) return true;
+    // (c) partial Gram matrix of the projected candidates over this CTA's rows
+    const int L = I.m - nP;
+    const int npair = KK * (KK + 1) / 2;
+    flops(PH_DM, 2.0 * npair * (double)L);
+    {
+      int q0, q1;
+      split(L, tm.size, tm.rank, q0, q1);
+      double* s_C = dyn;  // 32 x KK
+      double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      int pa[5], pb[5];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const int p = tid + s * NT;
+        pa[s] = -1;
+        pb[s] = -1;
+        if (p < npair) {
+          // pair p -> (a, b), a <= b, row-major upper triangle
+          int a = 0, rem = p;
+          while (rem >= KK - a) { rem -= KK - a; ++a; }
+          pa[s] = a;
+          pb[s] = a + rem;
+        }
+      }
+      for (int rb = q0; rb < q1; rb += 32) {
+        const int nr = min(32, q1 - rb);
+        __syncthreads();
+        for (int e = tid; e < nr * KK; e += NT) {
+          const int rr = e / KK, a = e - rr * KK;
+          s_C[rr * KK + a] = ldcg(Wcol(s_J[a]) + nP + rb + rr);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+          if (pa[s] < 0) continue;
+          double t = acc[s];
+          for (int rr = 0; rr < nr; ++rr) t = fma(s_C[rr * KK + pa[s]], s_C[rr * KK + pb[s]], t);
+          acc[s] = t;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 5; ++s)
+        if (pa[s] >= 0) I.part[(size_t)tm.rank * PW + tid + s * NT] = acc[s];
+    }
+    if (!sync()) return false;
+    // (d) reduce the pairs (one warp per pair, lanes over CTAs)
+    {
+      const int gw = tm.rank * NW + warp, nwt = tm.size * NW;
+      for (int p = gw; p < npair; p += nwt) {
+        double s = 0.0;
+        for (int t = lane; t < tm.size; t += 32) s += ldcg(I.part + (size_t)t * PW + p);
+        s = warp_sum(s);
+        if (lane == 0) {
+          int a = 0, rem = p;
+          while (rem >= KK - a) { rem -= KK - a; ++a; }
+          const int bb = a + rem;
+          I.Gm[a * KM + bb] = s;
+          I.Gm[bb * KM + a] = s;
+        }
+      }
+    }
+    if (!sync()) return false;
+    // (e) cosine test and greedy selection (every CTA, identical)
+    {
+      __shared__ double s_d[KM];
+      __shared__ unsigned long long s_mask[KM];
+      if (tid < KK) {
+        s_d[tid] = sqrt(ldcg(I.Gm + tid * KM + tid));
+        s_mask[tid] = 0ull;
+      }
+      __syncthreads();
+      for (int p = tid; p < KK * KK; p += NT) {
+        const int a = p / KK, l = p - a * KK;
+        if (l >= a) continue;
+        const double theta = ldcg(I.Gm + a * KM + l) / (s_d[a] * s_d[l]);
+        if (fabs(theta) < I.prm.delta) atomicOr(&s_mask[a], 1ull << l);
+      }
+      __syncthreads();
+      __shared__ int s_sel[KM];
+      __shared__ int s_nsel;
+      if (tid == 0) {
+        unsigned long long jm = 1ull;
+        int ns = 1;
+        s_sel[0] = 0;
+        for (int a = 1; a < KK; ++a)
+          if ((s_mask[a] & jm) == jm) {
+            jm |= 1ull << a;
+            s_sel[ns++] = a;
+          }
+        s_nsel = ns;
+      }
+      __syncthreads();
+      const int ns = s_nsel;
+      int pick = -1;
+      if (tid < ns) pick = s_J[s_sel[tid]];
+      __syncthreads();
+      if (tid < ns) s_J[tid] = pick;
+      kk = ns;
+      __syncthreads();
+    }
+    return true;
+  }
+
+  // ------------------------------------------------------------ panel
+  // Algorithm 4 on the trailing rows of the chosen columns: one Householder
+  // reflector per column in J order (house() as in the oracle), with T of
+  // the compact WY form accumulated alongside.  Rows are split over CTAs;
+  // each reflector costs one team barrier.
+  __device__ bool panel(const int* s_J) {
+    const int L = I.m - nP;
+    if (kk > L) kk = L;
+    int q0, q1;
+    split(L, tm.size, tm.rank, q0, q1);
+    double* V = I.V;
+    double* btp = I.rhs;  // panel copy of the trailing part of Q^T b
+    for (int e = tid; e < (q1 - q0) * kk; e += NT) {
+      const int rr = q0 + e / kk, t = e - (e / kk) * kk;
+      V[(size_t)rr * KM + t] = ldcg(Wcol(s_J[t]) + nP + rr);
+    }
+    for (int rr = q0 + tid; rr < q1; rr += NT) btp[rr] = ldcg(I.bt + nP + rr);
+    __syncthreads();  // the dots below read rows other threads just copied
+    __shared__ double s_sum[KM + 1];
+    __shared__ double s_f[KM + 1];
+    const int k0 = kk;
+    int i = 0;
+    for (; i < k0; ++i) {
+      // partial dots over own rows r > i: column i with every panel column and b
+      // (slots alternate with the parity of i: a fast CTA writing reflector
+      // i+1 must not overwrite what a slow CTA still reads for reflector i)
+      const int pb = (i & 1) * (KM + 1);
+      for (int l = warp; l <= k0; l += NW) {
+        double s = 0.0;
+        for (int rr = max(q0, i + 1) + lane; rr < q1; rr += 32) {
+          const double vi = ldcg(V + (size_t)rr * KM + i);
+          const double y = (l < k0) ? ldcg(V + (size_t)rr * KM + l) : ldcg(btp + rr);
+          s = fma(y, vi, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) I.part[(size_t)tm.rank * PW + pb + l] = s;
+      }
+      if (!sync()) return false;
+      if (tid <= k0) {
+        double s = 0.0;
+        for (int t = 0; t < tm.size; ++t) s += ldcg(I.part + (size_t)t * PW + pb + tid);
+        s_sum[tid] = s;
+      }
+      __syncthreads();
+      const double xii = ldcg(V + (size_t)i * KM + i);
+      const double alpha = sqrt(xii * xii + s_sum[i]);
+      const double an = ldcg(I.anorm + s_J[i]);
+      if (i >= L || !(alpha > (100.0 * EPS) * an)) break;
+      const double sg = (xii >= 0.0) ? 1.0 : -1.0;
+      const double v0 = xii + sg * alpha;
+      const double beta = 2.0 / (v0 * v0 + s_sum[i]);
+      if (tid <= k0) {
+        double f = 0.0;
+        if (tid > i && tid < k0) f = beta * (v0 * ldcg(V + (size_t)i * KM + tid) + s_sum[tid]);
+        if (tid == k0) f = beta * (v0 * ldcg(btp + i) + s_sum[k0]);
+        s_f[tid] = f;
+      }
+      __syncthreads();
+      // rank 0 records R22 row i, the panel right-hand side, v0, beta, T
+      if (tm.rank == 0) {
+        if (tid == i) I.R22[i + i * KM] = -sg * alpha;
+        if (tid > i && tid < k0) I.R22[i + tid * KM] = ldcg(V + (size_t)i * KM + tid) - s_f[tid] * v0;
+        if (tid == k0) I.pr[i] = ldcg(btp + i) - s_f[k0] * v0;
+        if (tid == 0) {
+          I.vtop[i] = v0;
+          I.beta[i] = beta;
+          I.T[i + i * KM] = beta;
+        }
+        // T[0:i, i] = -beta T[0:i, 0:i] z,  z_s = v_s^T v_i
+        __shared__ double s_z[KM];
+        if (tid < i) s_z[tid] = ldcg(V + (size_t)i * KM + tid) * v0 + s_sum[tid];
+        __syncthreads();
+        if (tid < i) {
+          double acc = 0.0;
+          for (int s = tid; s < i; ++s) acc = fma(ldcg(I.T + tid + s * KM), s_z[s], acc);
+          I.T[tid + i * KM] = -beta * acc;
+        }
+      }
+      flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i) + 1) * (double)(L - i));
+      // update own rows r > i of the later columns and of b
+      const int nl = k0 - i;  // columns i+1..k0-1 and b
+      for (int e = tid; e < (q1 - max(q0, i + 1)) * nl; e += NT) {
+        const int rr = max(q0, i + 1) + e / nl;
+        const int l = i + 1 + (e - (e / nl) * nl);
+        const double vi = ldcg(V + (size_t)rr * KM + i);
+        if (l < k0) V[(size_t)rr * KM + l] = ldcg(V + (size_t)rr * KM + l) - s_f[l] * vi;
+        else btp[rr] = ldcg(btp + rr) - s_f[k0] * vi;
+      }
+      __syncthreads();
+    }
+    kk = i;  // reflectors formed (truncated by the rank bound)
+    return sync();
+  }
+
+  // Back substitution with the kk x kk triangle R22 (one warp).
+  __device__ void solve_r22(int k, double* y) {
+    double a0 = (lane < k) ? ldcg(I.pr + lane) : 0.0;
+    double a1 = (lane + 32 < k) ? ldcg(I.pr + lane + 32) : 0.0;
+    double y0 = 0.0, y1 = 0.0;
+    for (int jj = k - 1; jj >= 0; --jj) {
+      const int owner = jj & 31;
+      const bool hi = jj >= 32;
+      double yv = 0.0;
+      if (lane == owner) yv = (hi ? a1 : a0) / ldcg(I.R22 + jj + jj * KM);
+      yv = __shfl_sync(0xffffffffu, yv, owner);
+      if (lane == owner) { if (hi) y1 = yv; else y0 = yv; }
+      if (lane < jj) a0 -= ldcg(I.R22 + lane + jj * KM) * yv;
+      if (lane + 32 < jj) a1 -= ldcg(I.R22 + lane + 32 + jj * KM) * yv;
+    }
+    if (lane < k) y[lane] = y0;
+    if (lane + 32 < k) y[lane + 32] = y1;
+  }
+
+  // Feasibility loop of Algorithm 3: drop the last J column while
+  // min y_J <= 0 (and |J| > 1).  y_J only depends on the R22 triangle.
+  __device__ bool feasibility() {
+    if (tm.rank == 0 && warp == 0) {
+      __shared__ double s_y[KM];
+      int k = kk, drops = 0;
+      for (;;) {
+        solve_r22(k, s_y);
+        __syncwarp();
+        double mn = INFINITY;
+        for (int t = lane; t < k; t += 32) mn = fmin(mn, s_y[t]);
+        mn = warp_max(-mn);
+        mn = -mn;
+        if (!(mn <= 0.0) || k <= 1) break;
+        --k;
+        ++drops;
+      }
+      for (int t = lane; t < k; t += 32) I.yJ[t] = s_y[t];
+      if (lane == 0) {
+        I.ctl[C_KP] = k;
+        I.ctl[C_DROPS] = drops;
+      }
+    }
+    if (!sync()) return false;
+    kp = ldcg(I.ctl + C_KP);
+    n_drop += ldcg(I.ctl + C_DROPS);
+    return true;
+  }
+
+  // ------------------------------------------------------------ triangular solve
+  // R y = rhs for positions [0, np) (blocked back substitution, one barrier
+  // per TB-block; rank 0 solves the diagonal blocks).  rhs is consumed.
+  __device__ bool trsv(int np) {
+    if (np <= 0) return true;
+    flops(cur_phase < 0 ? PH_SOLVE : cur_phase, (double)np * np);
+    const int nb = (np + TB - 1) / TB;
+    __shared__ double s_y[TB];
+    __shared__ double s_r[TB];
+    __shared__ int s_slot[TB];
+    for (int bi = nb - 1; bi >= 0; --bi) {
+      const int b0 = bi * TB, b1 = min(np, b0 + TB);
+      const bool has_next = bi + 1 < nb;
+      const int c0 = b0 + TB, c1 = min(np, c0 + TB);
+      if (has_next) {
+        if (tid < c1 - c0) {
+          s_y[tid] = ldcg(I.yP + c0 + tid);
+          s_slot[tid] = ldcg(I.rslot + c0 + tid);
+        }
+        __syncthreads();
+        // rows [0, b0): contribution of block bi+1 (spread over the team)
+        const int gt = tm.rank * NT + tid, nt = tm.size * NT;
+        for (int row = gt; row < b0; row += nt) {
+          double s = 0.0;
+          for (int j = 0; j < c1 - c0; ++j) s = fma(ldcg(Rcol(s_slot[j]) + row), s_y[j], s);
+          I.rhs[row] = ldcg(I.rhs + row) - s;
+        }
+      }
+      if (tm.rank == 0) {
+        // rows [b0, b1): contribution of block bi+1, then the diagonal block
+        if (tid < b1 - b0) {
+          double s = ldcg(I.rhs + b0 + tid);
+          if (has_next)
+            for (int j = 0; j < c1 - c0; ++j) s = fma(-ldcg(Rcol(s_slot[j]) + b0 + tid), s_y[j], s);
+          s_r[tid] = s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          double a0 = (lane < b1 - b0) ? s_r[lane] : 0.0;
+          double a1 = (lane + 32 < b1 - b0) ? s_r[lane + 32] : 0.0;
+          int sl0 = (lane < b1 - b0) ? ldcg(I.rslot + b0 + lane) : 0;
+          int sl1 = (lane + 32 < b1 - b0) ? ldcg(I.rslot + b0 + lane + 32) : 0;
+          for (int jj = b1 - b0 - 1; jj >= 0; --jj) {
+            const int owner = jj & 31;
+            const bool hi = jj >= 32;
+            const int slj = __shfl_sync(0xffffffffu, hi ? sl1 : sl0, owner);
+            const double* col = Rcol(slj);
+            double yv = 0.0;
+            if (lane == owner) yv = (hi ? a1 : a0) / ldcg(col + b0 + jj);
+            yv = __shfl_sync(0xffffffffu, yv, owner);
+            if (lane == owner) I.yP[b0 + jj] = yv;
+            if (lane < jj) a0 -= ldcg(col + b0 + lane) * yv;
+            if (lane + 32 < jj) a1 -= ldcg(col + b0 + lane + 32) * yv;
+          }
+        }
+      }
+      if (!sync()) return false;
+    }
+    return true;
+  }
+
+  // ------------------------------------------------------------ commit
+  // Makes J[0:kp] passive: new R columns [W(0:nP, J); R22], the block
+  // reflector I - V T^T V^T applied to the trailing rows of every Z column
+  // and of Q^T b, and u = ||C|| for the Z columns (Algorithm 3, rank-k update
+  // and column norms of C).
+  __device__ bool commit(const int* s_J) {
+    const int L = I.m - nP;
+    flops(PH_COMMIT, 4.0 * kp * (double)L * (double)(I.n - nP - kp + 1) + 2.0 * (double)L * (I.n - nP - kp));
+    // (a) R columns of the new positions (free slots rslot[nP..nP+kp))
+    {
+      const int gt = tm.rank * NT + tid, nt = tm.size * NT;
+      const int tot = (nP + KM) * kp;
+      for (int e = gt; e < tot; e += nt) {
+        const int t = e / (nP + KM), row = e - t * (nP + KM);
+        const int slot = ldcg(I.rslot + nP + t);
+        if (row < nP) Rcol(slot)[row] = ldcg(Wcol(s_J[t]) + row);
+        else if (row - nP <= t) Rcol(slot)[row] = ldcg(I.R22 + (row - nP) + t * KM);
+      }
+      if (tm.rank == 0 && tid < kp) {
+        I.order[nP + tid] = s_J[tid];
+        I.pos[s_J[tid]] = nP + tid;
+        I.xP[nP + tid] = 0.0;
+        I.yP[nP + tid] = ldcg(I.yJ + tid);
+      }
+    }
+    // (b) trailing update, one warp per Z column of this CTA's range (+ b)
+    double* s_V = dyn;                 // 32 rows x KM
+    double* s_dp = dyn + 32 * KM;      // NW x KM
+    __shared__ double s_T[KM * KM / 2 + KM];
+    __shared__ double s_vt[KM];
+    __shared__ int s_cols[NW];
+    // T^T staged once (upper triangle, column-major packed)
+    for (int e = tid; e < kp * kp; e += NT) {
+      const int t = e / kp, s = e - t * kp;
+      if (s <= t) s_T[t * (t + 1) / 2 + s] = ldcg(I.T + s + t * KM);
+    }
+    if (tid < kp) s_vt[tid] = ldcg(I.vtop + tid);
+    int c0, c1;
+    split(I.n, tm.size, tm.rank, c0, c1);
+    const bool do_b = (tm.rank == tm.size - 1);
+    __shared__ int s_list[CAND_LOCAL_MAX + 1];
+    __shared__ int s_nl;
+    if (tid == 0) s_nl = 0;
+    __syncthreads();
+    for (int c = c0 + tid; c < c1; c += NT) {
+      bool z = ldcg(I.pos + c) < 0;
+      for (int t = 0; t < kp && z; ++t) z = (s_J[t] != c);
+      if (z) {
+        const int k = atomicAdd(&s_nl, 1);
+        s_list[k] = c;
+      }
+    }
+    __syncthreads();
+    // deterministic order of the list is not needed: each column is independent
+    const int nl = s_nl + (do_b ? 1 : 0);
+    for (int base = 0; base < nl; base += NW) {
+      const int mine = base + warp;
+      const bool act = mine < nl;
+      int col_id = -2;
+      if (act) col_id = (mine < s_nl) ? s_list[mine] : -1;  // -1 = b
+      double* col = nullptr;
+      if (act) col = (col_id >= 0 ? Wcol(col_id) : I.bt) + nP;
+      if (lane == 0) s_cols[warp] = col_id;
+      // pass 1: d = V^T col (lanes over reflectors t = lane, lane + 32)
+      double d0 = 0.0, d1 = 0.0;
+      const int t0 = lane, t1 = lane + 32;
+      for (int rb = 0; rb < L; rb += 32) {
+        const int nr = min(32, L - rb);
+        __syncthreads();
+        for (int e = tid; e < nr * kp; e += NT) {
+          const int rr = e / kp, t = e - rr * kp;
+          s_V[rr * KM + t] = ldcg(I.V + (size_t)(rb + rr) * KM + t);
+        }
+        __syncthreads();
+        if (act) {
+          const double xr = (lane < nr) ? ldcg(col + rb + lane) : 0.0;
+          for (int rr = 0; rr < nr; ++rr) {
+            const double x = __shfl_sync(0xffffffffu, xr, rr);
+            const int rg = rb + rr;
+            if (t0 < kp && rg >= t0) d0 = fma((rg == t0) ? s_vt[t0] : s_V[rr * KM + t0], x, d0);
+            if (t1 < kp && rg >= t1) d1 = fma((rg == t1) ? s_vt[t1] : s_V[rr * KM + t1], x, d1);
+          }
+        }
+      }
+      // d' = T^T d
+      if (act) {
+        double e0 = 0.0, e1 = 0.0;
+        for (int s = 0; s < kp; ++s) {
+          const double ds = __shfl_sync(0xffffffffu, s < 32 ? d0 : d1, s & 31);
+          if (t0 < kp && s <= t0) e0 = fma(s_T[t0 * (t0 + 1) / 2 + s], ds, e0);
+          if (t1 < kp && s <= t1) e1 = fma(s_T[t1 * (t1 + 1) / 2 + s], ds, e1);
+        }
+        if (t0 < kp) s_dp[warp * KM + t0] = e0;
+        if (t1 < kp) s_dp[warp * KM + t1] = e1;
+      }
+      __syncwarp();
+      // pass 2: col -= V d' (lanes over rows), ||col[kp:L]||^2
+      double nrm = 0.0;
+      for (int rb = 0; rb < L; rb += 32) {
+        const int nr = min(32, L - rb);
+        __syncthreads();
+        for (int e = tid; e < nr * kp; e += NT) {
+          const int rr = e / kp, t = e - rr * kp;
+          s_V[rr * KM + t] = ldcg(I.V + (size_t)(rb + rr) * KM + t);
+        }
+        __syncthreads();
+        if (act && lane < nr) {
+          const int rg = rb + lane;
+          double x = ldcg(col + rg);
+          const int tmax = min(rg, kp - 1);
+          for (int t = 0; t <= tmax; ++t) {
+            const double vt = (t == rg) ? s_vt[t] : s_V[lane * KM + t];
+            x = fma(-vt, s_dp[warp * KM + t], x);
+          }
+          col[rg] = x;
+          if (rg >= kp) nrm = fma(x, x, nrm);
+        }
+      }
+      if (act) {
+        nrm = warp_sum(nrm);
+        if (lane == 0 && col_id >= 0) I.u[col_id] = sqrt(nrm);
+      }
+    }
+    nP += kp;
+    return sync();
+  }
+
+  // ------------------------------------------------------------ inner loop
+  // Algorithm 3 inner loop: step length alpha, x update, removal set Q,
+  // Givens downdate (Algorithm 5, one deleted position at a time from the
+  // highest), re-solve.
+  __device__ bool inner_loop() {
+    __shared__ double shv[32];
+    __shared__ int shi[32];
+    int steps = 0;
+    for (;;) {
+      // any y_P <= 0 ?
+      int neg = 0;
+      for (int p = tid; p < nP; p += NT) neg |= (ldcg(I.yP + p) <= 0.0);
+      neg = block_sum_int(neg, shi);
+      if (!neg) return true;
+      if (steps > nP + 1) {
+        status = LHDM_ERR_MAX_ITER;
+        return true;
+      }
+      ++steps;
+      ++n_inner;
+      // alpha = min x_p/(x_p - y_p) over y_p <= 0; i* lowest column on ties
+      ArgMax best{0.0, -1};
+      for (int p = tid; p < nP; p += NT) {
+        const double yp = ldcg(I.yP + p);
+        if (yp <= 0.0) {
+          const double xp = ldcg(I.xP + p);
+          const double t = xp / (xp - yp);
+          const int c = ldcg(I.order + p);
+          // minimise t: use (-t, c) in the argmax with lowest-index ties
+          best = amax_merge(best, ArgMax{-t, c});
+        }
+      }
+      best = block_amax(best, shv, shi);
+      const double alpha = -best.v;
+      const int istar = best.i;
+      // x update and removal set (rank 0 writes; positions listed descending)
+      __shared__ int s_nq;
+      int* qlist = I.qlist;
+      if (tm.rank == 0) {
+        if (tid == 0) s_nq = 0;
+        __syncthreads();
+        for (int p = tid; p < nP; p += NT) {
+          const double xp = ldcg(I.xP + p), yp = ldcg(I.yP + p);
+          double xn = xp + alpha * (yp - xp);
+          if (ldcg(I.order + p) == istar) xn = 0.0;
+          if (xn <= 0.0) {
+            xn = 0.0;
+            const int k = atomicAdd(&s_nq, 1);
+            qlist[k] = p;
+          }
+          I.xP[p] = xn;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          // sort descending (few entries)
+          const int nq = s_nq;
+          for (int a = 1; a < nq; ++a) {
+            const int v = qlist[a];
+            int bb = a - 1;
+            while (bb >= 0 && qlist[bb] < v) { qlist[bb + 1] = qlist[bb]; --bb; }
+            qlist[bb + 1] = v;
+          }
+          I.ctl[C_NRUN] = nq;
+        }
+      }
+      if (!sync()) return false;
+      const int nq = ldcg(I.ctl + C_NRUN);
+      removed += nq;
+      ++inner_step;
+      for (int k = 0; k < nq; ++k) {
+        const int q = ldcg(I.qlist + k);
+        if (!delete_position(q)) return false;
+      }
+      u_dirty = true;
+      // re-solve: rhs = (Q^T b)[0:nP] was written by the owner of b
+      if (!trsv(nP)) return false;
+    }
+  }
+
+  // Deletes position q of R (Algorithm 5 for one column): bookkeeping, the
+  // rotation chain over positions q..nP-2 generated in blocks of DB
+  // positions (block b on CTA b mod size, handed over through a published
+  // counter), then the same rotations applied to every Z column and to b.
+  __device__ bool delete_position(int q) {
+    const int np = nP;
+    const int nrot = np - 1 - q;
+    flops(PH_INNER, 3.0 * (double)nrot * (nrot + 1) + 6.0 * (double)nrot * (double)(I.n - np + 2));
+    if (tm.rank == 0) {
+      // the removed column re-enters Z in trailing form: W(:, c) = [R(0:q, slot); 0]
+      const int c = ldcg(I.order + q);
+      const int sq = ldcg(I.rslot + q);
+      double* wc = Wcol(c);
+      for (int i = tid; i < I.m; i += NT) wc[i] = (i <= q) ? ldcg(Rcol(sq) + i) : 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        I.pos[c] = -1;
+        for (int p = q; p < np - 1; ++p) {
+          const int oc = ldcg(I.order + p + 1);
+          I.rslot[p] = ldcg(I.rslot + p + 1);
+          I.order[p] = oc;
+          I.xP[p] = ldcg(I.xP + p + 1);
+          I.pos[oc] = p;
+        }
+        I.rslot[np - 1] = sq;
+        I.order[np - 1] = -1;
+        I.xP[np - 1] = 0.0;
+        I.ctl[C_READY] = 0;
+      }
+    }
+    if (!sync()) return false;
+    // rotation chain on R, warp 0 of the CTA owning each block
+    const int nblk = (nrot + DB - 1) / DB;
+    for (int blk = tm.rank; blk < nblk; blk += tm.size) {
+      if (warp != 0) continue;
+      const int bs = q + blk * DB;
+      const int pl = bs + lane;
+      const bool act = pl < np - 1;
+      double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
+      double carry = act ? ldcg(col + q) : 0.0;
+      // rotations of earlier blocks, as they are published
+      int t = q;
+      bool expired = false;
+      while (t < bs) {
+        int avail = 0;
+        if (lane == 0) {
+          // an expired wait raises the team error flag; the next barrier
+          // then fails in every CTA
+          bool ok = wait_ge(I.ctl + C_READY, t - q + 1, tm_err());
+          avail = ok ? *(volatile int*)(I.ctl + C_READY) : -1;
+        }
+        avail = __shfl_sync(0xffffffffu, avail, 0);
+        if (avail < 0) { expired = true; break; }
+        const int tend = min(bs, q + avail);
+        for (; t < tend; ++t) {
+          const double cs = ldcg(I.rotc + (t - q)), sn = ldcg(I.rots + (t - q));
+          if (act) {
+            const double bot = ldcg(col + t + 1);
+            col[t] = cs * carry + sn * bot;
+            carry = -sn * carry + cs * bot;
+          }
+        }
+      }
+      if (expired) break;
+      // own block: generate one rotation per position, publish it
+      const int bend = min(bs + DB, np - 1);
+      for (t = bs; t < bend; ++t) {
+        const int owner = t - bs;
+        double cs = 1.0, sn = 0.0;
+        if (lane == owner) {
+          const double a = carry, bb = ldcg(col + t + 1);
+          const double rr = sqrt(a * a + bb * bb);
+          if (rr != 0.0) { cs = a / rr; sn = bb / rr; }
+          col[t] = rr;
+          col[t + 1] = 0.0;
+          I.rotc[t - q] = cs;
+          I.rots[t - q] = sn;
+          __threadfence();
+          atomicExch(I.ctl + C_READY, t - q + 1);
+        }
+        cs = __shfl_sync(0xffffffffu, cs, owner);
+        sn = __shfl_sync(0xffffffffu, sn, owner);
+        if (lane > owner && act) {
+          const double bot = ldcg(col + t + 1);
+          col[t] = cs * carry + sn * bot;
+          carry = -sn * carry + cs * bot;
+        }
+      }
+    }
+    if (!sync()) return false;
+    nP = np - 1;
+    // the same rotations on every Z column (carry scan over rows q..np-1) and b
+    {
+      double* s_c = dyn;
+      double* s_s = dyn + ROT_STAGE;
+      int c0, c1;
+      split(I.n, tm.size, tm.rank, c0, c1);
+      const bool do_b = (tm.rank == tm.size - 1);
+      const int ncols = (c1 - c0) + (do_b ? 1 : 0);
+      for (int base = 0; base < ncols; base += NT) {
+        const int k = base + tid;
+        double* colp = nullptr;
+        if (k < ncols) {
+          if (k < c1 - c0) {
+            const int c = c0 + k;
+            if (ldcg(I.pos + c) < 0) colp = Wcol(c);
+          } else {
+            colp = I.bt;
+          }
+        }
+        double carry = colp ? ldcg(colp + q) : 0.0;
+        for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
+          const int ns = min(ROT_STAGE, nrot - rb);
+          __syncthreads();
+          for (int e = tid; e < ns; e += NT) {
+            s_c[e] = ldcg(I.rotc + rb + e);
+            s_s[e] = ldcg(I.rots + rb + e);
+          }
+          __syncthreads();
+          if (colp) {
+            int e = 0;
+            for (; e + 4 <= ns; e += 4) {
+              const int t = q + rb + e;
+              const double b0 = ldcg(colp + t + 1), b1 = ldcg(colp + t + 2);
+              const double b2 = ldcg(colp + t + 3), b3 = ldcg(colp + t + 4);
+              double cs = s_c[e], sn = s_s[e];
+              colp[t] = cs * carry + sn * b0;
+              carry = -sn * carry + cs * b0;
+              cs = s_c[e + 1]; sn = s_s[e + 1];
+              colp[t + 1] = cs * carry + sn * b1;
+              carry = -sn * carry + cs * b1;
+              cs = s_c[e + 2]; sn = s_s[e + 2];
+              colp[t + 2] = cs * carry + sn * b2;
+              carry = -sn * carry + cs * b2;
+              cs = s_c[e + 3]; sn = s_s[e + 3];
+              colp[t + 3] = cs * carry + sn * b3;
+              carry = -sn * carry + cs * b3;
+            }
+            for (; e < ns; ++e) {
+              const int t = q + rb + e;
+              const double bot = ldcg(colp + t + 1);
+              const double cs = s_c[e], sn = s_s[e];
+              colp[t] = cs * carry + sn * bot;
+              carry = -sn * carry + cs * bot;
+            }
+          }
+        }
+        if (colp) colp[np - 1] = carry;
+      }
+      // the triangular solve that follows reads rhs = (Q^T b)[0:nP]
+      if (do_b) {
+        __syncthreads();
+        for (int p = tid; p < nP; p += NT) I.rhs[p] = ldcg(I.bt + p);
+      }
+    }
+    return sync();
+  }
+
+  __device__ int* tm_err();
+
+  // ------------------------------------------------------------ residual and dual
+  // r = b - A_P x_P (row tiles of 32 rows, warps split the positions).
+  __device__ void residual() {
+    __shared__ double s_acc[NW][32];
+    double rs = 0.0;
+    const int ntile = (I.m + 31) / 32;
+    for (int tile = tm.rank; tile < ntile; tile += tm.size) {
+      const int row = tile * 32 + lane;
+      double acc = 0.0;
+      if (row < I.m)
+        for (int p = warp; p < nP; p += NW) {
+          const int c = ldcg(I.order + p);
+          acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
+        }
+      s_acc[warp][lane] = acc;
+      __syncthreads();
+      if (warp == 0 && row < I.m) {
+        double s = 0.0;
+        for (int k = 0; k < NW; ++k) s += s_acc[k][lane];
+        const double rv = __ldg(I.b + row) - s;
+        I.r[row] = rv;
+        rs = fma(rv, rv, rs);
+      }
+      __syncthreads();
+    }
+    // x = y on P
+    const int gt = tm.rank * NT + tid, nt = tm.size * NT;
+    for (int p = gt; p < nP; p += nt) I.xP[p] = ldcg(I.yP + p);
+    __shared__ double sh[32];
+    rs = block_sum(rs, sh);
+    if (tid == 0) I.part[(size_t)tm.rank * PW + P_RS] = rs;
+  }
+
+  // w = A^T r on Z (w_P = 0), u refreshed after removals, O1 partial.
+  __device__ void dual() {
+    int c0, c1;
+    split(I.n, tm.size, tm.rank, c0, c1);
+    for (int c = c0 + warp; c < c1; c += NW) {
+      if (ldcg(I.pos + c) >= 0) {
+        if (lane == 0) I.w[c] = 0.0;
+        continue;
+      }
+      const double* a = I.A + (size_t)c * I.lda;
+      double s = 0.0;
+      for (int i = lane; i < I.m; i += 32) s = fma(__ldg(a + i), ldcg(I.r + i), s);
+      s = warp_sum(s);
+      double un = 0.0;
+      if (u_dirty) {
+        const double* wc = Wcol(c);
+        for (int i = nP + lane; i < I.m; i += 32) {
+          const double v = ldcg(wc + i);
+          un = fma(v, v, un);
+        }
+        un = warp_sum(un);
+      }
+      if (lane == 0) {
+        I.w[c] = s;
+        if (u_dirty) I.u[c] = sqrt(un);
+      }
+    }
+    // resid sum of squares of this CTA is in part[PW-1]; fold it into slot 6
+    const double rs = ldcg(I.part + (size_t)tm.rank * PW + P_RS);
+    o1_partial(0.0, rs, 0.0);
+  }
+
+  // ------------------------------------------------------------ outputs
+  __device__ bool finish() {
+    __shared__ int shi[32];
+    // x and the sorted passive set
+    int c0, c1;
+    split(I.n, tm.size, tm.rank, c0, c1);
+    int cnt = 0;
+    for (int c = c0 + tid; c < c1; c += NT) {
+      const int p = ldcg(I.pos + c);
+      I.x_out[c] = (p >= 0 && status != LHDM_ERR_NONFINITE) ? ldcg(I.xP + p) : 0.0;
+      cnt += (p >= 0);
+    }
+    cnt = block_sum_int(cnt, shi);
+    if (tid == 0) I.ipart[tm.rank * 8] = cnt;
+    if (!sync()) return false;
+    __shared__ int s_base;
+    if (tid == 0) {
+      int acc = 0;
+      for (int t = 0; t < tm.rank; ++t) acc += ldcg(I.ipart + t * 8);
+      s_base = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int k = s_base;
+      for (int c = c0; c < c1; ++c)
+        if (ldcg(I.pos + c) >= 0) I.passive_out[k++] = c;
+    }
+    const int gt = tm.rank * NT + tid, nt = tm.size * NT;
+    for (int p = nP + gt; p < I.n; p += nt) I.passive_out[p] = -1;
+    if (tm.rank == 0 && tid == 0) {
+      lhdm_info inf;
+      inf.status = status;
+      inf.n_outer = n_outer;
+      inf.n_inner = n_inner;
+      inf.n_drop = n_drop;
+      inf.n_passive = nP;
+      inf.rank_limited = rank_limited;
+      inf.resid_norm = sqrt(rsq);
+      inf.max_wZ = wz_any;
+      inf.tol_w = tol_w;
+      *I.info_out = inf;
+      *I.nP_out = nP;
+      if (I.phase_ns) {
+        phase(-1);
+        for (int i = 0; i < NPHASE; ++i) {
+          I.phase_ns[i] = ph[i];
+          I.phase_ns[NPHASE + i] = fl[i];
+        }
+      }
+    }
+    return true;
+  }
+
+  // ------------------------------------------------------------ the solve
+  __device__ void run() {
+    phase(PH_SETUP);
+    setup();
+    flops(PH_SETUP, 4.0 * (double)I.m * I.n);
+    if (!sync()) return fail_out();
+    o1_reduce(true);
+    tol_w = (I.prm.tol_w >= 0.0) ? I.prm.tol_w
+                                 : 10.0 * EPS * (double)max(I.m, I.n) * amax * sqrt(bsq);
+    if (nonfinite) {
+      status = LHDM_ERR_NONFINITE;
+      nP = 0;
+      for (int c = tm.rank * NT + tid; c < I.n; c += tm.size * NT) I.pos[c] = -1;
+      if (!sync()) return fail_out();
+      finish();
+      return;
+    }
+    __shared__ int s_J[KM];
+    const int max_outer = I.prm.max_outer > 0 ? I.prm.max_outer : 3 * I.n;
+    for (;;) {
+      if (n_elig == 0 || !(wmax > tol_w)) {
+        if (wz_any > tol_w) rank_limited = 1;
+        break;
+      }
+      if (n_outer >= max_outer) {
+        status = LHDM_ERR_MAX_ITER;
+        break;
+      }
+      phase(PH_DM);
+      if (!dm_select(s_J)) return fail_out();
+      kdm = kk;
+      phase(PH_PANEL);
+      if (!panel(s_J)) return fail_out();
+      if (kk == 0) {
+        rank_limited = 1;
+        break;
+      }
+      phase(PH_SOLVE);
+      if (!feasibility()) return fail_out();
+      // y_P: rhs = (Q^T b)[0:nP] - R12 y_J, then back substitution
+      {
+        __shared__ double s_yj[KM];
+        if (tid < kp) s_yj[tid] = ldcg(I.yJ + tid);
+        __syncthreads();
+        const int gt = tm.rank * NT + tid, nt = tm.size * NT;
+        for (int p = gt; p < nP; p += nt) {
+          double s = ldcg(I.bt + p);
+          for (int t = 0; t < kp; ++t) s = fma(-ldcg(Wcol(s_J[t]) + p), s_yj[t], s);
+          I.rhs[p] = s;
+        }
+      }
+      flops(PH_SOLVE, 2.0 * nP * (double)kp + (double)kk * kk);
+      if (!sync()) return fail_out();
+      if (!trsv(nP)) return fail_out();
+      phase(PH_COMMIT);
+      if (!commit(s_J)) return fail_out();
+      phase(PH_INNER);
+      u_dirty = false;
+      removed = 0;
+      inner_step = 0;
+      if (!inner_loop()) return fail_out();
+      if (status != LHDM_OK) break;
+      phase(PH_RESID);
+      flops(PH_RESID, 2.0 * (double)I.m * nP);
+      residual();
+      if (!sync()) return fail_out();
+      phase(PH_DUAL);
+      flops(PH_DUAL, (u_dirty ? 4.0 : 2.0) * (double)I.m * (double)(I.n - nP));
+      dual();
+      if (!sync()) return fail_out();
+      if (I.trace && tm.rank == 0 && tid == 0 && n_outer < I.trace_cap) {
+        int* tr = I.trace + 6 * n_outer;
+        tr[0] = kdm;
+        tr[1] = kp;
+        tr[2] = inner_step;
+        tr[3] = nP;
+        tr[4] = removed;
+        tr[5] = s_J[0];
+      }
+      o1_reduce(false);
+      ++n_outer;
+    }
+    phase(PH_SETUP);
+    finish();
+  }
+
+  __device__ void fail_out() {
+    // a bounded wait expired: report and leave without further barriers
+    if (tm.rank == 0 && tid == 0) {
+      lhdm_info inf;
+      inf.status = LHDM_ERR_TIMEOUT;
+      inf.n_outer = n_outer;
+      inf.n_inner = n_inner;
+      inf.n_drop = n_drop;
+      inf.n_passive = nP;
+      inf.rank_limited = rank_limited;
+      inf.resid_norm = -1.0;
+      inf.max_wZ = 0.0;
+      inf.tol_w = tol_w;
+      *I.info_out = inf;
+      *I.nP_out = 0;
+    }
+  }
+};
+
+template <>
+__device__ __forceinline__ int* Engine<GridTeam>::tm_err() { return tm.err; }
+template <>
+__device__ __forceinline__ int* Engine<CtaTeam>::tm_err() { return nullptr; }
+
+}  // namespace lhdm

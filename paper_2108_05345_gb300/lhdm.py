@@ -1,0 +1,296 @@
+"""Python binding of liblhdm.so (include/lhdm.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels; PyTorch supplies
+device memory and streams.  The library must have been built (build.py);
+importing this module on a machine without it raises instead of falling
+back to anything else.
+
+Matrices are column-major FP64: pass A as a (m, n) torch tensor with
+stride (1, lda), e.g. ``colmajor(A)``.
+"""
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+LHDM_OK = 0
+LHDM_ERR_INVALID_ARG = 1
+LHDM_ERR_MAX_ITER = 2
+LHDM_ERR_NONFINITE = 4
+LHDM_ERR_CUDA = 5
+LHDM_ERR_TIMEOUT = 6
+LHDM_ERR_ALLOC = 7
+LHDM_ERR_NO_STATE = 8
+KMAX_LIMIT = 64
+PHASES = ("setup", "dm", "panel", "solve", "commit", "inner", "residual", "dual")
+
+
+class Params(C.Structure):
+    _fields_ = [("tau1", C.c_double), ("tau2", C.c_double), ("delta", C.c_double),
+                ("tol_w", C.c_double), ("k_max", C.c_int32), ("max_outer", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_outer", C.c_int32), ("n_inner", C.c_int32),
+                ("n_drop", C.c_int32), ("n_passive", C.c_int32), ("rank_limited", C.c_int32),
+                ("resid_norm", C.c_double), ("max_wZ", C.c_double), ("tol_w", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads liblhdm.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("liblhdm.so is not built; run paper_2108_05345_gb300/build.py "
+                               "(or __graft_entry__.build()) on a machine with nvcc")
+        L = C.CDLL(_build.LIB)
+        P, I, V = C.POINTER(Params), C.POINTER(Info), C.c_void_p
+        d, i32 = C.c_void_p, C.c_int32
+        L.lhdm_default_params.argtypes = [P]
+        L.lhdm_status_string.argtypes = [C.c_int]
+        L.lhdm_status_string.restype = C.c_char_p
+        L.lhdm_create.argtypes = [C.POINTER(V), i32, i32]
+        L.lhdm_destroy.argtypes = [V]
+        L.lhdm_solve.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
+        L.lhdm_solve_host.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
+        L.lhdm_get_info.argtypes = [V, I, V]
+        L.lhdm_backward.argtypes = [V, d, i32, d, d, d, i32, V]
+        L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
+        L.lhdm_trace.argtypes = [V, C.POINTER(C.c_int32), i32, V]
+        L.lhdm_debug_state.argtypes = [V, C.c_char_p, C.c_void_p, C.c_int64, V]
+        pp = C.POINTER(C.c_void_p)
+        ip = C.POINTER(C.c_int32)
+        L.lhdm_batch_create.argtypes = [C.POINTER(V), i32, ip, ip, ip, pp, pp, pp, pp, d, P, V]
+        L.lhdm_batch_run.argtypes = [V, V]
+        L.lhdm_batch_backward.argtypes = [V, pp, pp, pp, ip, V]
+        L.lhdm_batch_kmax.argtypes = [V, i32]
+        L.lhdm_batch_destroy.argtypes = [V]
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().lhdm_status_string(int(s)).decode()
+
+
+def _check(rc, what):
+    if rc != LHDM_OK:
+        raise RuntimeError("%s failed: %s (%d)" % (what, status_string(rc), rc))
+
+
+def default_params(**kw):
+    p = Params()
+    lib().lhdm_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def colmajor(A):
+    """(m, n) tensor -> the same values with column-major strides (1, m)."""
+    return A.t().contiguous().t()
+
+
+def _lda(A):
+    m, n = A.shape
+    if A.dtype != torch.float64:
+        raise TypeError("A must be float64")
+    if m == 0 or n == 0:
+        return max(1, m)  # no element is read
+    if n == 1 and A.stride(0) == 1:
+        return max(1, m)
+    if m == 1 and A.stride(1) >= 1:
+        return A.stride(1)  # a single row: the column stride is the leading dimension
+    if A.stride(0) != 1 or A.stride(1) < max(1, m):
+        raise ValueError("A must be column-major (stride (1, lda >= m)); use colmajor(A)")
+    return A.stride(1)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A solve context for problems up to max_m x max_n (lhdm_create)."""
+
+    def __init__(self, max_m, max_n):
+        h = C.c_void_p()
+        _check(lib().lhdm_create(C.byref(h), int(max_m), int(max_n)), "lhdm_create")
+        self.h = h
+        self.max_m, self.max_n = int(max_m), int(max_n)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhdm_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def solve(self, A, b, params=None, x=None, passive=None, stream=None, sync=True):
+        """lhdm_solve on device tensors; returns (x, passive, info dict or None)."""
+        m, n = A.shape
+        lda = _lda(A)
+        if b.dtype != torch.float64 or b.numel() != m or not b.is_contiguous():
+            raise ValueError("b must be a contiguous float64 vector of length m")
+        if x is None:
+            x = torch.empty(n, dtype=torch.float64, device=A.device)
+        if passive is None:
+            passive = torch.empty(n, dtype=torch.int32, device=A.device)
+        info = Info() if sync else None
+        rc = lib().lhdm_solve(self.h, m, n, A.data_ptr(), lda, b.data_ptr(),
+                              C.byref(params) if params is not None else None,
+                              x.data_ptr(), passive.data_ptr(),
+                              C.byref(info) if info is not None else None, _stream(stream))
+        _check(rc, "lhdm_solve")
+        return x, passive, (info.as_dict() if info is not None else None)
+
+    def solve_host(self, A, b, params=None, stream=None):
+        """lhdm_solve_host on host arrays (numpy, Fortran order or any layout
+        with unit row stride); returns (x, passive, info dict)."""
+        import numpy as np
+        A = np.asfortranarray(A, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        m, n = A.shape
+        x = np.empty(n, dtype=np.float64)
+        p = np.empty(n, dtype=np.int32)
+        info = Info()
+        rc = lib().lhdm_solve_host(self.h, m, n, A.ctypes.data, max(1, m), b.ctypes.data,
+                                   C.byref(params) if params is not None else None,
+                                   x.ctypes.data, p.ctypes.data, C.byref(info), _stream(stream))
+        _check(rc, "lhdm_solve_host")
+        return x, p, info.as_dict()
+
+    def solve_host_ptr(self, m, n, A_ptr, lda, b_ptr, x_ptr, p_ptr, params=None, stream=None):
+        """lhdm_solve_host on raw host pointers (e.g. pinned torch tensors)."""
+        info = Info()
+        rc = lib().lhdm_solve_host(self.h, m, n, A_ptr, lda, b_ptr,
+                                   C.byref(params) if params is not None else None,
+                                   x_ptr, p_ptr, C.byref(info), _stream(stream))
+        _check(rc, "lhdm_solve_host")
+        return info.as_dict()
+
+    def info(self, stream=None):
+        inf = Info()
+        _check(lib().lhdm_get_info(self.h, C.byref(inf), _stream(stream)), "lhdm_get_info")
+        return inf.as_dict()
+
+    def backward(self, A, dLdx, want_db=True, want_dA=True, stream=None):
+        """lhdm_backward for the last solve; returns (dL/db, dL/dA)."""
+        m, n = A.shape
+        lda = _lda(A)
+        db = torch.empty(m, dtype=torch.float64, device=A.device) if want_db else None
+        dA = colmajor(torch.empty(m, n, dtype=torch.float64, device=A.device)) if want_dA else None
+        rc = lib().lhdm_backward(self.h, A.data_ptr(), lda, dLdx.contiguous().data_ptr(),
+                                 db.data_ptr() if db is not None else None,
+                                 dA.data_ptr() if dA is not None else None, max(1, m), _stream(stream))
+        _check(rc, "lhdm_backward")
+        return db, dA
+
+    def trace(self, stream=None):
+        """Per outer step: |J| from DM, |J| kept, inner steps, |P| after,
+        removed, first column of J (lhdm_trace)."""
+        import numpy as np
+        cap = 3 * self.max_n + 8
+        buf = (C.c_int32 * (6 * cap))()
+        k = lib().lhdm_trace(self.h, buf, cap, _stream(stream))
+        if k < 0:
+            raise RuntimeError("lhdm_trace failed")
+        return np.frombuffer(buf, dtype=np.int32)[: 6 * k].reshape(k, 6).copy()
+
+    def state(self, name, count, stream=None):
+        """lhdm_debug_state: a named piece of the solver state as numpy."""
+        import numpy as np
+        dt = np.int32 if name in ("order", "rslot", "pos") else np.float64
+        out = np.empty(int(count), dtype=dt)
+        _check(lib().lhdm_debug_state(self.h, name.encode(), out.ctypes.data, int(count), _stream(stream)),
+               "lhdm_debug_state")
+        return out
+
+    def phase_times(self, stream=None):
+        """{phase: ms} of the last solve (lhdm_phase_times)."""
+        return self.profile(stream)[0]
+
+    def profile(self, stream=None):
+        """({phase: ms}, {phase: algorithmic FP64 flops}) of the last solve."""
+        n = 2 * len(PHASES)
+        buf = (C.c_double * n)()
+        k = lib().lhdm_phase_times(self.h, buf, n, _stream(stream))
+        if k < n:
+            raise RuntimeError("lhdm_phase_times failed")
+        ms = {PHASES[i]: buf[i] for i in range(len(PHASES))}
+        fl = {PHASES[i]: buf[len(PHASES) + i] for i in range(len(PHASES))}
+        return ms, fl
+
+
+class Batch:
+    """A planned batch of independent solves (lhdm_batch_create); run() is
+    one persistent launch and may be captured in a CUDA graph."""
+
+    def __init__(self, As, bs, params=None, stream=None):
+        self.As = As
+        self.bs = bs
+        k = len(As)
+        self.k = k
+        dev = As[0].device if k else torch.device("cuda")
+        self.xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A in As]
+        self.ps = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in As]
+        self.infos = torch.zeros(max(k, 1) * C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
+        m = (C.c_int32 * max(k, 1))(*[A.shape[0] for A in As])
+        n = (C.c_int32 * max(k, 1))(*[A.shape[1] for A in As])
+        lda = (C.c_int32 * max(k, 1))(*[_lda(A) for A in As])
+        ptrs = lambda ts: (C.c_void_p * max(k, 1))(*[t.data_ptr() for t in ts])
+        self._keep = (m, n, lda)
+        h = C.c_void_p()
+        rc = lib().lhdm_batch_create(C.byref(h), k, m, n, lda, ptrs(As), ptrs(bs), ptrs(self.xs),
+                                     ptrs(self.ps), self.infos.data_ptr(),
+                                     C.byref(params) if params is not None else None, _stream(stream))
+        _check(rc, "lhdm_batch_create")
+        self.h = h
+
+    def run(self, stream=None):
+        _check(lib().lhdm_batch_run(self.h, _stream(stream)), "lhdm_batch_run")
+
+    def info(self):
+        raw = self.infos.cpu().numpy().tobytes()
+        out = []
+        for i in range(self.k):
+            inf = Info.from_buffer_copy(raw[i * C.sizeof(Info):(i + 1) * C.sizeof(Info)])
+            out.append(inf.as_dict())
+        return out
+
+    def kmax(self, i):
+        return lib().lhdm_batch_kmax(self.h, i)
+
+    def backward(self, dLdx, want_db=True, want_dA=True, stream=None):
+        k = self.k
+        dbs = [torch.empty(A.shape[0], dtype=torch.float64, device=A.device) for A in self.As] if want_db else None
+        dAs = [colmajor(torch.empty(A.shape, dtype=torch.float64, device=A.device)) for A in self.As] if want_dA else None
+        ptrs = lambda ts: (C.c_void_p * max(k, 1))(*[t.data_ptr() for t in ts])
+        ld = (C.c_int32 * max(k, 1))(*[max(1, A.shape[0]) for A in self.As])
+        gs = [g.contiguous() for g in dLdx]  # kept alive across the call
+        rc = lib().lhdm_batch_backward(self.h, ptrs(gs),
+                                       ptrs(dbs) if dbs else None, ptrs(dAs) if dAs else None, ld,
+                                       _stream(stream))
+        _check(rc, "lhdm_batch_backward")
+        return dbs, dAs
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhdm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
