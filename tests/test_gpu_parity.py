@@ -52,10 +52,10 @@ TIE = 1e-9
 
 def first_divergence(tr_gpu, tr_ref, margin):
     for s in range(min(len(tr_gpu), len(tr_ref))):
+        if margin[s] < TIE:
+            return None  # step s took a decision by rounding: paths may part here
         if not np.array_equal(tr_gpu[s], tr_ref[s]):
             return s, tr_gpu[s].tolist(), tr_ref[s].tolist()
-        if margin[s] < TIE:
-            return None
     if len(tr_gpu) != len(tr_ref):
         return len(tr_ref), None, None
     return None
