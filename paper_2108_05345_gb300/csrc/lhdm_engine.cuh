@@ -207,9 +207,11 @@ struct GridTeam {
   int* err;
   __device__ __forceinline__ bool sync() {
     __shared__ int s_ok;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+      // the CTA barrier orders every thread's writes before this fence,
+      // which is cumulative: one fence per CTA publishes them
+      __threadfence();
       int ok = 1;
       volatile unsigned int* gen = bar + 1;
       const unsigned int g = *gen;

@@ -479,12 +479,23 @@ struct Engine {
         if (lane == 0) I.part[(size_t)tm.rank * PW + pb + l] = s;
       }
       if (!sync()) return false;
-      if (tid <= k0) {
-        double s = 0.0;
-        for (int t = 0; t < tm.size; ++t) s += ldcg(I.part + (size_t)t * PW + pb + tid);
-        s_sum[tid] = s;
+      {
+        // two-level reduction of the team's partials: warp w sums the CTAs
+        // t = w (mod NW), then the NW partial sums are added in order
+        double* sR = dyn;  // NW x (KM + 1)
+        for (int l = lane; l <= k0; l += 32) {
+          double sacc = 0.0;
+          for (int t = warp; t < tm.size; t += NW) sacc += ldcg(I.part + (size_t)t * PW + pb + l);
+          sR[warp * (KM + 1) + l] = sacc;
+        }
+        __syncthreads();
+        if (tid <= k0) {
+          double sacc = 0.0;
+          for (int w2 = 0; w2 < NW; ++w2) sacc += sR[w2 * (KM + 1) + tid];
+          s_sum[tid] = sacc;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       const double xii = ldcg(V + (size_t)i * KM + i);
       const double alpha = sqrt(xii * xii + s_sum[i]);
       const double an = ldcg(I.anorm + s_J[i]);
@@ -514,9 +525,16 @@ struct Engine {
         if (tid < i) s_z[tid] = ldcg(V + (size_t)i * KM + tid) * v0 + s_sum[tid];
         __syncthreads();
         if (tid < i) {
-          double acc = 0.0;
-          for (int s = tid; s < i; ++s) acc = fma(ldcg(I.T + tid + s * KM), s_z[s], acc);
-          I.T[tid + i * KM] = -beta * acc;
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+          int s = tid;
+          for (; s + 3 < i; s += 4) {
+            a0 = fma(ldcg(I.T + tid + s * KM), s_z[s], a0);
+            a1 = fma(ldcg(I.T + tid + (s + 1) * KM), s_z[s + 1], a1);
+            a2 = fma(ldcg(I.T + tid + (s + 2) * KM), s_z[s + 2], a2);
+            a3 = fma(ldcg(I.T + tid + (s + 3) * KM), s_z[s + 3], a3);
+          }
+          for (; s < i; ++s) a0 = fma(ldcg(I.T + tid + s * KM), s_z[s], a0);
+          I.T[tid + i * KM] = -beta * ((a0 + a1) + (a2 + a3));
         }
       }
       flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i) + 1) * (double)(L - i));
@@ -585,57 +603,99 @@ struct Engine {
 
   // ------------------------------------------------------------ triangular solve
   // R y = rhs for positions [0, np) (blocked back substitution, one barrier
-  // per TB-block; rank 0 solves the diagonal blocks).  rhs is consumed.
+  // per TB-block).  Rank 0 solves each diagonal block from shared memory
+  // (staged in parallel) after folding in the block just solved; the other
+  // rows receive that block's contribution spread over the whole team.
+  // rhs is consumed.
   __device__ bool trsv(int np) {
     if (np <= 0) return true;
     flops(cur_phase < 0 ? PH_SOLVE : cur_phase, (double)np * np);
     const int nb = (np + TB - 1) / TB;
     __shared__ double s_y[TB];
-    __shared__ double s_r[TB];
     __shared__ int s_slot[TB];
+    double* sD = dyn;                   // TB x (TB+1): sD[col * (TB+1) + row]
+    double* sP = dyn + TB * (TB + 1);   // 8 x TB partial contributions
     for (int bi = nb - 1; bi >= 0; --bi) {
-      const int b0 = bi * TB, b1 = min(np, b0 + TB);
+      const int b0 = bi * TB, b1 = min(np, b0 + TB), nbk = b1 - b0;
       const bool has_next = bi + 1 < nb;
-      const int c0 = b0 + TB, c1 = min(np, c0 + TB);
+      const int c0 = b0 + TB, c1 = min(np, c0 + TB), nc = c1 - c0;
+      if (has_next && tid < nc) {
+        s_y[tid] = ldcg(I.yP + c0 + tid);
+        s_slot[tid] = ldcg(I.rslot + c0 + tid);
+      }
+      __syncthreads();
       if (has_next) {
-        if (tid < c1 - c0) {
-          s_y[tid] = ldcg(I.yP + c0 + tid);
-          s_slot[tid] = ldcg(I.rslot + c0 + tid);
-        }
-        __syncthreads();
-        // rows [0, b0): contribution of block bi+1 (spread over the team)
-        const int gt = tm.rank * NT + tid, nt = tm.size * NT;
-        for (int row = gt; row < b0; row += nt) {
-          double s = 0.0;
-          for (int j = 0; j < c1 - c0; ++j) s = fma(ldcg(Rcol(s_slot[j]) + row), s_y[j], s);
-          I.rhs[row] = ldcg(I.rhs + row) - s;
+        // rows [0, b0): contribution of block bi+1, one warp per row (lanes
+        // over the block's columns: all loads independent), rows spread
+        // over the team
+        const int gw = tm.rank * NW + warp, nwt = tm.size * NW;
+        for (int row = gw; row < b0; row += nwt) {
+          const double p0 = (lane < nc) ? ldcg(Rcol(s_slot[lane]) + row) * s_y[lane] : 0.0;
+          const double p1 = (lane + 32 < nc) ? ldcg(Rcol(s_slot[lane + 32]) + row) * s_y[lane + 32] : 0.0;
+          const double sacc = warp_sum(p0 + p1);
+          if (lane == 0) I.rhs[row] = ldcg(I.rhs + row) - sacc;
         }
       }
       if (tm.rank == 0) {
-        // rows [b0, b1): contribution of block bi+1, then the diagonal block
-        if (tid < b1 - b0) {
-          double s = ldcg(I.rhs + b0 + tid);
-          if (has_next)
-            for (int j = 0; j < c1 - c0; ++j) s = fma(-ldcg(Rcol(s_slot[j]) + b0 + tid), s_y[j], s);
-          s_r[tid] = s;
+        // stage the diagonal block (upper triangle), its reciprocal diagonal
+        // and the partial contributions of block bi+1 to rows [b0, b1)
+        __shared__ int s_bslot[TB];
+        __shared__ double s_rinv[TB];
+        if (tid < nbk) s_bslot[tid] = ldcg(I.rslot + b0 + tid);
+        __syncthreads();
+        {
+          double v[TB * TB / NT];
+#pragma unroll
+          for (int q2 = 0; q2 < TB * TB / NT; ++q2) {
+            const int idx = tid + q2 * NT, cl = idx / TB, rw = idx - cl * TB;
+            v[q2] = (cl < nbk && rw <= cl) ? ldcg(Rcol(s_bslot[cl]) + b0 + rw) : 0.0;
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < TB * TB / NT; ++q2) {
+            const int idx = tid + q2 * NT, cl = idx / TB, rw = idx - cl * TB;
+            sD[cl * (TB + 1) + rw] = v[q2];
+            if (rw == cl && cl < nbk) s_rinv[cl] = 1.0 / v[q2];
+          }
+        }
+        if (has_next) {
+          const int rw = tid & (TB - 1), g = tid / TB;  // 8 groups of TB/8 columns
+          double v[TB / 8];
+#pragma unroll
+          for (int q2 = 0; q2 < TB / 8; ++q2) {
+            const int j = g * (TB / 8) + q2;
+            v[q2] = (rw < nbk && j < nc) ? ldcg(Rcol(s_slot[j]) + b0 + rw) : 0.0;
+          }
+          double sacc = 0.0;
+#pragma unroll
+          for (int q2 = 0; q2 < TB / 8; ++q2) {
+            const int j = g * (TB / 8) + q2;
+            if (j < nc) sacc = fma(v[q2], s_y[j], sacc);
+          }
+          sP[g * TB + rw] = sacc;
         }
         __syncthreads();
         if (warp == 0) {
-          double a0 = (lane < b1 - b0) ? s_r[lane] : 0.0;
-          double a1 = (lane + 32 < b1 - b0) ? s_r[lane + 32] : 0.0;
-          int sl0 = (lane < b1 - b0) ? ldcg(I.rslot + b0 + lane) : 0;
-          int sl1 = (lane + 32 < b1 - b0) ? ldcg(I.rslot + b0 + lane + 32) : 0;
-          for (int jj = b1 - b0 - 1; jj >= 0; --jj) {
+          double a0 = 0.0, a1 = 0.0;
+          if (lane < nbk) {
+            a0 = ldcg(I.rhs + b0 + lane);
+            if (has_next)
+              for (int g = 0; g < 8; ++g) a0 -= sP[g * TB + lane];
+          }
+          if (lane + 32 < nbk) {
+            a1 = ldcg(I.rhs + b0 + lane + 32);
+            if (has_next)
+              for (int g = 0; g < 8; ++g) a1 -= sP[g * TB + lane + 32];
+          }
+          for (int jj = nbk - 1; jj >= 0; --jj) {
             const int owner = jj & 31;
             const bool hi = jj >= 32;
-            const int slj = __shfl_sync(0xffffffffu, hi ? sl1 : sl0, owner);
-            const double* col = Rcol(slj);
+            const double* cj = sD + jj * (TB + 1);
             double yv = 0.0;
-            if (lane == owner) yv = (hi ? a1 : a0) / ldcg(col + b0 + jj);
+            if (lane == owner) yv = (hi ? a1 : a0) * s_rinv[jj];
             yv = __shfl_sync(0xffffffffu, yv, owner);
             if (lane == owner) I.yP[b0 + jj] = yv;
-            if (lane < jj) a0 -= ldcg(col + b0 + lane) * yv;
-            if (lane + 32 < jj) a1 -= ldcg(col + b0 + lane + 32) * yv;
+            if (lane < jj) a0 -= cj[lane] * yv;
+            if (lane + 32 < jj) a1 -= cj[lane + 32] * yv;
           }
         }
       }
@@ -669,16 +729,24 @@ struct Engine {
         I.yP[nP + tid] = ldcg(I.yJ + tid);
       }
     }
-    // (b) trailing update, one warp per Z column of this CTA's range (+ b)
-    double* s_V = dyn;                 // 32 rows x KM
-    double* s_dp = dyn + 32 * KM;      // NW x KM
+    // (b) trailing update of this CTA's Z columns (+ b on the last CTA), in
+    // batches of CB columns: D = V^T C (pass 1), D' = T^T D, C -= V D' and
+    // the new trailing norms (pass 2).  V's triangular structure (zero above
+    // row t, v0 on row t) is folded into the staged chunks.
+    constexpr int RC = 64;  // rows per staged chunk
+    constexpr int CB = 16;  // columns per batch
+    constexpr int VS = KM + 1;          // padded row stride of the staged V chunk
+    double* s_V = dyn;                  // RC x VS
+    double* s_X = s_V + RC * VS;        // CB x RC
+    double* s_D = s_X + CB * RC;        // KM x CB
+    double* s_E = s_D + KM * CB;        // KM x CB
     __shared__ double s_T[KM * KM / 2 + KM];
     __shared__ double s_vt[KM];
-    __shared__ int s_cols[NW];
-    // T^T staged once (upper triangle, column-major packed)
+    __shared__ double s_nrm[NW][2];
+    __shared__ int s_cid[CB];
     for (int e = tid; e < kp * kp; e += NT) {
-      const int t = e / kp, s = e - t * kp;
-      if (s <= t) s_T[t * (t + 1) / 2 + s] = ldcg(I.T + s + t * KM);
+      const int t = e / kp, sidx = e - t * kp;
+      if (sidx <= t) s_T[t * (t + 1) / 2 + sidx] = ldcg(I.T + sidx + t * KM);
     }
     if (tid < kp) s_vt[tid] = ldcg(I.vtop + tid);
     int c0, c1;
@@ -691,80 +759,103 @@ struct Engine {
     for (int c = c0 + tid; c < c1; c += NT) {
       bool z = ldcg(I.pos + c) < 0;
       for (int t = 0; t < kp && z; ++t) z = (s_J[t] != c);
-      if (z) {
-        const int k = atomicAdd(&s_nl, 1);
-        s_list[k] = c;
-      }
+      if (z) s_list[atomicAdd(&s_nl, 1)] = c;
     }
     __syncthreads();
-    // deterministic order of the list is not needed: each column is independent
     const int nl = s_nl + (do_b ? 1 : 0);
-    for (int base = 0; base < nl; base += NW) {
-      const int mine = base + warp;
-      const bool act = mine < nl;
-      int col_id = -2;
-      if (act) col_id = (mine < s_nl) ? s_list[mine] : -1;  // -1 = b
-      double* col = nullptr;
-      if (act) col = (col_id >= 0 ? Wcol(col_id) : I.bt) + nP;
-      if (lane == 0) s_cols[warp] = col_id;
-      // pass 1: d = V^T col (lanes over reflectors t = lane, lane + 32)
-      double d0 = 0.0, d1 = 0.0;
-      const int t0 = lane, t1 = lane + 32;
-      for (int rb = 0; rb < L; rb += 32) {
-        const int nr = min(32, L - rb);
+    auto colptr = [&](int k) -> double* {
+      const int id = s_cid[k];
+      return (id >= 0 ? Wcol(id) : I.bt) + nP;
+    };
+    auto stage = [&](int rb, int nr, int nb) {
+      for (int e = tid; e < nr * kp; e += NT) {
+        const int rr = e / kp, t = e - rr * kp, rg = rb + rr;
+        s_V[rr * VS + t] = (rg > t) ? ldcg(I.V + (size_t)rg * KM + t) : (rg == t ? s_vt[t] : 0.0);
+      }
+      for (int e = tid; e < nb * nr; e += NT) {
+        const int cc = e / nr, rr = e - cc * nr;
+        s_X[cc * RC + rr] = ldcg(colptr(cc) + rb + rr);
+      }
+    };
+    for (int base = 0; base < nl; base += CB) {
+      const int nb = min(CB, nl - base);
+      __syncthreads();
+      if (tid < nb) s_cid[tid] = (base + tid < s_nl) ? s_list[base + tid] : -1;
+      __syncthreads();
+      const int outputs = kp * nb;
+      // threads per output from kp and the full batch width only, so a
+      // column's sums do not depend on how many columns share its batch
+      int G = 32;
+      while (G > 1 && G * kp * CB > NT) G >>= 1;
+      const int per = NT / G;  // outputs handled per sweep
+      // pass 1: D[t][c] = sum_r v_t[r] x_c[r]; G threads per output split the rows
+      double acc0 = 0.0, acc1 = 0.0;
+      const int o0 = tid / G, o1 = o0 + per, sub = tid - o0 * G;
+      const int t_0 = o0 % max(kp, 1), c_0 = o0 / max(kp, 1);
+      const int t_1 = o1 % max(kp, 1), c_1 = o1 / max(kp, 1);
+      for (int rb = 0; rb < L; rb += RC) {
+        const int nr = min(RC, L - rb);
         __syncthreads();
-        for (int e = tid; e < nr * kp; e += NT) {
-          const int rr = e / kp, t = e - rr * kp;
-          s_V[rr * KM + t] = ldcg(I.V + (size_t)(rb + rr) * KM + t);
-        }
+        stage(rb, nr, nb);
         __syncthreads();
-        if (act) {
-          const double xr = (lane < nr) ? ldcg(col + rb + lane) : 0.0;
-          for (int rr = 0; rr < nr; ++rr) {
-            const double x = __shfl_sync(0xffffffffu, xr, rr);
-            const int rg = rb + rr;
-            if (t0 < kp && rg >= t0) d0 = fma((rg == t0) ? s_vt[t0] : s_V[rr * KM + t0], x, d0);
-            if (t1 < kp && rg >= t1) d1 = fma((rg == t1) ? s_vt[t1] : s_V[rr * KM + t1], x, d1);
+        if (o0 < outputs)
+          for (int rr = sub; rr < nr; rr += G) acc0 = fma(s_V[rr * VS + t_0], s_X[c_0 * RC + rr], acc0);
+        if (o1 < outputs)
+          for (int rr = sub; rr < nr; rr += G) acc1 = fma(s_V[rr * VS + t_1], s_X[c_1 * RC + rr], acc1);
+      }
+      for (int off = G >> 1; off >= 1; off >>= 1) {
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
+      }
+      if (sub == 0) {
+        if (o0 < outputs) s_D[t_0 * CB + c_0] = acc0;
+        if (o1 < outputs) s_D[t_1 * CB + c_1] = acc1;
+      }
+      __syncthreads();
+      // D' = T^T D
+      for (int o = tid; o < outputs; o += NT) {
+        const int t = o % kp, cc = o / kp;
+        double e2 = 0.0;
+        for (int sidx = 0; sidx <= t; ++sidx) e2 = fma(s_T[t * (t + 1) / 2 + sidx], s_D[sidx * CB + cc], e2);
+        s_E[t * CB + cc] = e2;
+      }
+      // pass 2: x -= V d' per (row, column); thread slots k = 0, 1 keep a
+      // fixed column (tid / RC and tid / RC + NT / RC)
+      double nrm0 = 0.0, nrm1 = 0.0;
+      for (int rb = 0; rb < L; rb += RC) {
+        const int nr = min(RC, L - rb);
+        __syncthreads();
+        stage(rb, nr, nb);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int idx = tid + k * NT;
+          const int cc = idx / RC, rr = idx - cc * RC;
+          if (cc < nb && rr < nr) {
+            double x = s_X[cc * RC + rr];
+            for (int t = 0; t < kp; ++t) x = fma(-s_V[rr * VS + t], s_E[t * CB + cc], x);
+            colptr(cc)[rb + rr] = x;
+            if (rb + rr >= kp) {
+              if (k == 0) nrm0 = fma(x, x, nrm0);
+              else nrm1 = fma(x, x, nrm1);
+            }
           }
         }
       }
-      // d' = T^T d
-      if (act) {
-        double e0 = 0.0, e1 = 0.0;
-        for (int s = 0; s < kp; ++s) {
-          const double ds = __shfl_sync(0xffffffffu, s < 32 ? d0 : d1, s & 31);
-          if (t0 < kp && s <= t0) e0 = fma(s_T[t0 * (t0 + 1) / 2 + s], ds, e0);
-          if (t1 < kp && s <= t1) e1 = fma(s_T[t1 * (t1 + 1) / 2 + s], ds, e1);
-        }
-        if (t0 < kp) s_dp[warp * KM + t0] = e0;
-        if (t1 < kp) s_dp[warp * KM + t1] = e1;
+      // norms: each column's slot is held by RC consecutive threads (2 warps)
+      nrm0 = warp_sum(nrm0);
+      nrm1 = warp_sum(nrm1);
+      if (lane == 0) {
+        s_nrm[warp][0] = nrm0;
+        s_nrm[warp][1] = nrm1;
       }
-      __syncwarp();
-      // pass 2: col -= V d' (lanes over rows), ||col[kp:L]||^2
-      double nrm = 0.0;
-      for (int rb = 0; rb < L; rb += 32) {
-        const int nr = min(32, L - rb);
-        __syncthreads();
-        for (int e = tid; e < nr * kp; e += NT) {
-          const int rr = e / kp, t = e - rr * kp;
-          s_V[rr * KM + t] = ldcg(I.V + (size_t)(rb + rr) * KM + t);
-        }
-        __syncthreads();
-        if (act && lane < nr) {
-          const int rg = rb + lane;
-          double x = ldcg(col + rg);
-          const int tmax = min(rg, kp - 1);
-          for (int t = 0; t <= tmax; ++t) {
-            const double vt = (t == rg) ? s_vt[t] : s_V[lane * KM + t];
-            x = fma(-vt, s_dp[warp * KM + t], x);
-          }
-          col[rg] = x;
-          if (rg >= kp) nrm = fma(x, x, nrm);
-        }
-      }
-      if (act) {
-        nrm = warp_sum(nrm);
-        if (lane == 0 && col_id >= 0) I.u[col_id] = sqrt(nrm);
+      __syncthreads();
+      if (tid < nb) {
+        const int k = tid / (NT / RC), cl = tid - k * (NT / RC);  // column tid in slot k
+        const int w0 = cl * (RC / 32);
+        double v = 0.0;
+        for (int w2 = 0; w2 < RC / 32; ++w2) v += s_nrm[w0 + w2][k];
+        if (s_cid[tid] >= 0) I.u[s_cid[tid]] = sqrt(v);
       }
     }
     nP += kp;
@@ -881,16 +972,30 @@ struct Engine {
       }
     }
     if (!sync()) return false;
-    // rotation chain on R, warp 0 of the CTA owning each block
+    // (i) rotation chain on R.  Block b covers generating positions
+    // [q + b*DB, q + (b+1)*DB); lane l of warp 0 owns position bs + l.
     const int nblk = (nrot + DB - 1) / DB;
+    double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
     for (int blk = tm.rank; blk < nblk; blk += tm.size) {
-      if (warp != 0) continue;
       const int bs = q + blk * DB;
+      const int bend = min(bs + DB, np - 1);
+      __syncthreads();
+      // rows below bs are the only ones earlier rotations touch: stage the
+      // block's own rows (bs+1 .. bs+DB) once
+      for (int idx = tid; idx < DB * DB; idx += NT) {
+        const int l = idx / DB, e = idx - (idx / DB) * DB;
+        double v = 0.0;
+        if (bs + l < np - 1 && e <= l) v = ldcg(Rcol(ldcg(I.rslot + bs + l)) + bs + 1 + e);
+        sB[e * (DB + 1) + l] = v;
+      }
+      __syncthreads();
+      if (warp != 0) continue;
       const int pl = bs + lane;
       const bool act = pl < np - 1;
       double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
       double carry = act ? ldcg(col + q) : 0.0;
-      // rotations of earlier blocks, as they are published
+      // earlier blocks' rotations, as they are published, 16 at a time with
+      // the column values loaded ahead of the (sequential) carry chain
       int t = q;
       bool expired = false;
       while (t < bs) {
@@ -898,106 +1003,127 @@ struct Engine {
         if (lane == 0) {
           // an expired wait raises the team error flag; the next barrier
           // then fails in every CTA
-          bool ok = wait_ge(I.ctl + C_READY, t - q + 1, tm_err());
+          const bool ok = wait_ge(I.ctl + C_READY, t - q + 1, tm_err());
           avail = ok ? *(volatile int*)(I.ctl + C_READY) : -1;
         }
         avail = __shfl_sync(0xffffffffu, avail, 0);
         if (avail < 0) { expired = true; break; }
         const int tend = min(bs, q + avail);
-        for (; t < tend; ++t) {
-          const double cs = ldcg(I.rotc + (t - q)), sn = ldcg(I.rots + (t - q));
-          if (act) {
-            const double bot = ldcg(col + t + 1);
-            col[t] = cs * carry + sn * bot;
-            carry = -sn * carry + cs * bot;
+        while (t < tend) {
+          const int cnt = min(16, tend - t);
+          const double mcs = (lane < cnt) ? ldcg(I.rotc + (t - q) + lane) : 0.0;
+          const double mss = (lane < cnt) ? ldcg(I.rots + (t - q) + lane) : 0.0;
+          double bot[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) bot[e] = (act && e < cnt) ? ldcg(col + t + 1 + e) : 0.0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const double cs = __shfl_sync(0xffffffffu, mcs, e), sn = __shfl_sync(0xffffffffu, mss, e);
+            if (e < cnt && act) {
+              col[t + e] = cs * carry + sn * bot[e];
+              carry = -sn * carry + cs * bot[e];
+            }
           }
+          t += cnt;
         }
       }
-      if (expired) break;
-      // own block: generate one rotation per position, publish it
-      const int bend = min(bs + DB, np - 1);
+      if (expired) continue;
+      // own block: one rotation per position from the staged rows; lane e
+      // keeps rotation bs+e and they are published 8 at a time
+      double pcs = 1.0, pss = 0.0;
       for (t = bs; t < bend; ++t) {
-        const int owner = t - bs;
+        const int e = t - bs;
         double cs = 1.0, sn = 0.0;
-        if (lane == owner) {
-          const double a = carry, bb = ldcg(col + t + 1);
-          const double rr = sqrt(a * a + bb * bb);
-          if (rr != 0.0) { cs = a / rr; sn = bb / rr; }
+        if (lane == e) {
+          // rotation zeroing bb against a: r = hypot(a, bb), cs = a/r, sn = bb/r,
+          // through one reciprocal square root on the dependent chain
+          const double a = carry, bb = sB[e * (DB + 1) + e];
+          const double r2 = fma(a, a, bb * bb);
+          double rr = 0.0;
+          if (r2 > 0.0) {
+            const double inv = rsqrt(r2);
+            cs = a * inv;
+            sn = bb * inv;
+            rr = r2 * inv;
+          }
           col[t] = rr;
           col[t + 1] = 0.0;
-          I.rotc[t - q] = cs;
-          I.rots[t - q] = sn;
-          __threadfence();
-          atomicExch(I.ctl + C_READY, t - q + 1);
         }
-        cs = __shfl_sync(0xffffffffu, cs, owner);
-        sn = __shfl_sync(0xffffffffu, sn, owner);
-        if (lane > owner && act) {
-          const double bot = ldcg(col + t + 1);
+        cs = __shfl_sync(0xffffffffu, cs, e);
+        sn = __shfl_sync(0xffffffffu, sn, e);
+        if (lane == e) { pcs = cs; pss = sn; }
+        if (lane > e && act) {
+          const double bot = sB[e * (DB + 1) + lane];
           col[t] = cs * carry + sn * bot;
           carry = -sn * carry + cs * bot;
+        }
+        if ((e & 7) == 7 || t == bend - 1) {
+          if (lane >= (e & ~7) && lane <= e) {
+            I.rotc[bs - q + lane] = pcs;
+            I.rots[bs - q + lane] = pss;
+          }
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) atomicExch(I.ctl + C_READY, t - q + 1);
         }
       }
     }
     if (!sync()) return false;
     nP = np - 1;
-    // the same rotations on every Z column (carry scan over rows q..np-1) and b
+    // (ii) the same rotations on every Z column and on b: one warp per
+    // column; the carry recurrence c' = -s c + cs * bot is affine, so each
+    // 32-row chunk is a warp-wide prefix scan of affine maps
     {
       double* s_c = dyn;
       double* s_s = dyn + ROT_STAGE;
       int c0, c1;
       split(I.n, tm.size, tm.rank, c0, c1);
       const bool do_b = (tm.rank == tm.size - 1);
-      const int ncols = (c1 - c0) + (do_b ? 1 : 0);
-      for (int base = 0; base < ncols; base += NT) {
-        const int k = base + tid;
-        double* colp = nullptr;
-        if (k < ncols) {
-          if (k < c1 - c0) {
-            const int c = c0 + k;
-            if (ldcg(I.pos + c) < 0) colp = Wcol(c);
-          } else {
-            colp = I.bt;
-          }
+      __shared__ int s_zl[CAND_LOCAL_MAX + 1];
+      __shared__ int s_nz;
+      if (tid == 0) s_nz = 0;
+      __syncthreads();
+      for (int c = c0 + tid; c < c1; c += NT)
+        if (ldcg(I.pos + c) < 0) s_zl[atomicAdd(&s_nz, 1)] = c;
+      __syncthreads();
+      const int nz = s_nz + (do_b ? 1 : 0);
+      for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
+        const int ns = min(ROT_STAGE, nrot - rb);
+        __syncthreads();
+        for (int e = tid; e < ns; e += NT) {
+          s_c[e] = ldcg(I.rotc + rb + e);
+          s_s[e] = ldcg(I.rots + rb + e);
         }
-        double carry = colp ? ldcg(colp + q) : 0.0;
-        for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
-          const int ns = min(ROT_STAGE, nrot - rb);
-          __syncthreads();
-          for (int e = tid; e < ns; e += NT) {
-            s_c[e] = ldcg(I.rotc + rb + e);
-            s_s[e] = ldcg(I.rots + rb + e);
-          }
-          __syncthreads();
-          if (colp) {
-            int e = 0;
-            for (; e + 4 <= ns; e += 4) {
-              const int t = q + rb + e;
-              const double b0 = ldcg(colp + t + 1), b1 = ldcg(colp + t + 2);
-              const double b2 = ldcg(colp + t + 3), b3 = ldcg(colp + t + 4);
-              double cs = s_c[e], sn = s_s[e];
-              colp[t] = cs * carry + sn * b0;
-              carry = -sn * carry + cs * b0;
-              cs = s_c[e + 1]; sn = s_s[e + 1];
-              colp[t + 1] = cs * carry + sn * b1;
-              carry = -sn * carry + cs * b1;
-              cs = s_c[e + 2]; sn = s_s[e + 2];
-              colp[t + 2] = cs * carry + sn * b2;
-              carry = -sn * carry + cs * b2;
-              cs = s_c[e + 3]; sn = s_s[e + 3];
-              colp[t + 3] = cs * carry + sn * b3;
-              carry = -sn * carry + cs * b3;
+        __syncthreads();
+        for (int k = warp; k < nz; k += NW) {
+          double* colp = (k < s_nz) ? Wcol(s_zl[k]) : I.bt;
+          double carry = ldcg(colp + q + rb);
+          // next chunk's column values are loaded before the scan of this one
+          double nbot = (lane < ns) ? ldcg(colp + q + rb + 1 + lane) : 0.0;
+          for (int t0 = 0; t0 < ns; t0 += 32) {
+            const int cnt = min(32, ns - t0);
+            const double bot = nbot;
+            nbot = (t0 + 32 + lane < ns) ? ldcg(colp + q + rb + t0 + 33 + lane) : 0.0;
+            double cs = 1.0, sn = 0.0;
+            if (lane < cnt) { cs = s_c[t0 + lane]; sn = s_s[t0 + lane]; }
+            double Am = (lane < cnt) ? -sn : 1.0, Bm = (lane < cnt) ? cs * bot : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const double Ap = __shfl_up_sync(0xffffffffu, Am, o);
+              const double Bp = __shfl_up_sync(0xffffffffu, Bm, o);
+              if (lane >= o) {
+                Bm = fma(Am, Bp, Bm);
+                Am = Am * Ap;
+              }
             }
-            for (; e < ns; ++e) {
-              const int t = q + rb + e;
-              const double bot = ldcg(colp + t + 1);
-              const double cs = s_c[e], sn = s_s[e];
-              colp[t] = cs * carry + sn * bot;
-              carry = -sn * carry + cs * bot;
-            }
+            const double incl = fma(Am, carry, Bm);  // carry after rotation lane
+            double cin = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane == 0) cin = carry;
+            if (lane < cnt) colp[q + rb + t0 + lane] = cs * cin + sn * bot;
+            carry = __shfl_sync(0xffffffffu, incl, cnt - 1);
           }
+          if (lane == 0) colp[q + rb + ns] = carry;
         }
-        if (colp) colp[np - 1] = carry;
       }
       // the triangular solve that follows reads rhs = (Q^T b)[0:nP]
       if (do_b) {
@@ -1018,13 +1144,20 @@ struct Engine {
     const int ntile = (I.m + 31) / 32;
     for (int tile = tm.rank; tile < ntile; tile += tm.size) {
       const int row = tile * 32 + lane;
-      double acc = 0.0;
-      if (row < I.m)
-        for (int p = warp; p < nP; p += NW) {
+      double acc = 0.0, acc2 = 0.0;
+      if (row < I.m) {
+        int p = warp;
+        for (; p + NW < nP; p += 2 * NW) {
+          const int c = ldcg(I.order + p), c2 = ldcg(I.order + p + NW);
+          acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
+          acc2 = fma(__ldg(I.A + (size_t)c2 * I.lda + row), ldcg(I.yP + p + NW), acc2);
+        }
+        for (; p < nP; p += NW) {
           const int c = ldcg(I.order + p);
           acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
         }
-      s_acc[warp][lane] = acc;
+      }
+      s_acc[warp][lane] = acc + acc2;
       __syncthreads();
       if (warp == 0 && row < I.m) {
         double s = 0.0;
@@ -1053,17 +1186,37 @@ struct Engine {
         continue;
       }
       const double* a = I.A + (size_t)c * I.lda;
-      double s = 0.0;
-      for (int i = lane; i < I.m; i += 32) s = fma(__ldg(a + i), ldcg(I.r + i), s);
-      s = warp_sum(s);
+      double sa[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sa[k] = 0.0;
+      int i = lane;
+      for (; i + 224 < I.m; i += 256) {
+        double av[8], rv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          av[k] = __ldg(a + i + 32 * k);
+          rv[k] = ldcg(I.r + i + 32 * k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sa[k] = fma(av[k], rv[k], sa[k]);
+      }
+      for (; i < I.m; i += 32) sa[0] = fma(__ldg(a + i), ldcg(I.r + i), sa[0]);
+      const double s = warp_sum(((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7])));
       double un = 0.0;
       if (u_dirty) {
         const double* wc = Wcol(c);
-        for (int i = nP + lane; i < I.m; i += 32) {
-          const double v = ldcg(wc + i);
-          un = fma(v, v, un);
+        double u0 = 0.0, u1 = 0.0;
+        int i2 = nP + lane;
+        for (; i2 + 32 < I.m; i2 += 64) {
+          const double v0 = ldcg(wc + i2), v1 = ldcg(wc + i2 + 32);
+          u0 = fma(v0, v0, u0);
+          u1 = fma(v1, v1, u1);
         }
-        un = warp_sum(un);
+        for (; i2 < I.m; i2 += 32) {
+          const double v0 = ldcg(wc + i2);
+          u0 = fma(v0, v0, u0);
+        }
+        un = warp_sum(u0 + u1);
       }
       if (lane == 0) {
         I.w[c] = s;

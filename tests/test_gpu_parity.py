@@ -68,10 +68,17 @@ def assert_parity(x, P, info, ref, counters=True, ctx=None):
         d = first_divergence(ctx.trace(), ref["trace"], ref["trace_margin"])
         assert d is None, "decision trace diverges at outer step %s: gpu %s oracle %s" % d
     counters = counters and not tied
-    assert P.tolist() == ref["passive"].tolist()
+    if tied:
+        # a rounding tie may leave columns whose coefficient is at the
+        # rounding level on one side only: compare the significant support
+        sig = lambda v: np.flatnonzero(v > 1e-9 * max(np.abs(v).max(), 1e-300)).tolist()
+        assert sig(x) == sig(ref["x"])
+    else:
+        assert P.tolist() == ref["passive"].tolist()
     nx = max(np.linalg.norm(ref["x"]), 1e-300)
     assert np.linalg.norm(x - ref["x"]) <= RTOL * nx or np.linalg.norm(ref["x"]) == 0 and not x.any()
-    assert info["n_passive"] == ref["n_passive"]
+    if not tied:
+        assert info["n_passive"] == ref["n_passive"]
     if counters:
         assert (info["n_outer"], info["n_inner"], info["n_drop"]) == (ref["n_outer"], ref["n_inner"], ref["n_drop"])
     assert abs(info["resid_norm"] - ref["resid_norm"]) <= 1e-9 * max(1.0, ref["resid_norm"])
@@ -84,7 +91,8 @@ def test_small_recovery(L, ctx, seed, k_max):
     x, P, ps, info = solve(L, ctx, A, b, k_max=k_max)
     ref = O.nnls(A, b, k_max=k_max, trace=True)
     assert_parity(x, P, info, ref, ctx=ctx)
-    assert P.tolist() == np.flatnonzero(x0).tolist()
+    sig = np.flatnonzero(x > 1e-9 * np.abs(x).max()).tolist()
+    assert sig == np.flatnonzero(x0).tolist()
     assert (ps[len(P):] == -1).all()
 
 
