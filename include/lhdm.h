@@ -179,10 +179,12 @@ int lhdm_trace(lhdm_ctx* ctx, int32_t* out, int32_t max_rows, void* stream);
  * arrays.  Errors: INVALID_ARG for an unknown name or count too large. */
 int lhdm_debug_state(lhdm_ctx* ctx, const char* name, void* host, int64_t count, void* stream);
 
-/* Profile of the last solve on ctx.  ms[0..8) = device time in ms of each
- * solver phase (setup, DM, panel, triangular solve, commit, inner loop,
- * residual, dual vector); ms[8..16) = the algorithmic FP64 flops of the same
- * phases (an FMA counts 2).  Writes min(n, 16) values and returns how many
+/* Profile of the last solve on ctx.  ms[0..12) = device time in ms of each
+ * solver phase: setup, DM, panel, triangular solve (outer step), commit,
+ * inner-loop control and bookkeeping, residual, dual vector, feasibility
+ * loop, Givens chain on R, rotations of the Z columns, triangular solves of
+ * the inner loop; ms[12..24) = the algorithmic FP64 flops of the same
+ * phases (an FMA counts 2).  Writes min(n, 24) values and returns how many
  * (negative status on error).  Synchronises the stream. */
 int lhdm_phase_times(lhdm_ctx* ctx, double* ms, int32_t n, void* stream);
 

@@ -496,6 +496,7 @@ int lhdm_get_info(lhdm_ctx* c, lhdm_info* info, void* stream) {
 }
 
 int lhdm_phase_times(lhdm_ctx* c, double* ms, int32_t n, void* stream) {
+  static_assert(NPHASE == 12, "phase list documented in lhdm.h");
   if (!c || !ms || n < 0) return -LHDM_ERR_INVALID_ARG;
   double h[2 * NPHASE];
   cudaStream_t st = (cudaStream_t)stream;

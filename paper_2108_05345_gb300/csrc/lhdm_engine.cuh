@@ -41,11 +41,14 @@ constexpr int P_O1 = PW - 16;
 constexpr int P_RS = PW - 1;
 constexpr int TB = 64;               // triangular-solve block
 constexpr int DB = 32;               // downdate block (positions per warp)
-constexpr int NPHASE = 8;
+constexpr int NPHASE = 12;
 constexpr double EPS = 2.220446049250313e-16;  // 2^-52
 constexpr long long WAIT_NS = 4000000000LL;    // bound on any device-side wait
 
-enum Phase { PH_SETUP = 0, PH_DM, PH_PANEL, PH_SOLVE, PH_COMMIT, PH_INNER, PH_RESID, PH_DUAL };
+enum Phase {
+  PH_SETUP = 0, PH_DM, PH_PANEL, PH_SOLVE, PH_COMMIT, PH_INNER, PH_RESID, PH_DUAL,
+  PH_FEAS, PH_CHAIN, PH_ZROT, PH_ITRSV
+};
 
 struct DevParams {
   double tau1, tau2, delta, tol_w;

@@ -557,12 +557,15 @@ struct Engine {
   __device__ void solve_r22(int k, double* y) {
     double a0 = (lane < k) ? ldcg(I.pr + lane) : 0.0;
     double a1 = (lane + 32 < k) ? ldcg(I.pr + lane + 32) : 0.0;
+    // reciprocal diagonal computed by all lanes at once, off the chain
+    const double r0 = (lane < k) ? 1.0 / ldcg(I.R22 + lane + lane * KM) : 0.0;
+    const double r1 = (lane + 32 < k) ? 1.0 / ldcg(I.R22 + (lane + 32) + (lane + 32) * KM) : 0.0;
     double y0 = 0.0, y1 = 0.0;
     for (int jj = k - 1; jj >= 0; --jj) {
       const int owner = jj & 31;
       const bool hi = jj >= 32;
       double yv = 0.0;
-      if (lane == owner) yv = (hi ? a1 : a0) / ldcg(I.R22 + jj + jj * KM);
+      if (lane == owner) yv = (hi ? a1 : a0) * (hi ? r1 : r0);
       yv = __shfl_sync(0xffffffffu, yv, owner);
       if (lane == owner) { if (hi) y1 = yv; else y0 = yv; }
       if (lane < jj) a0 -= ldcg(I.R22 + lane + jj * KM) * yv;
@@ -937,7 +940,9 @@ struct Engine {
       }
       u_dirty = true;
       // re-solve: rhs = (Q^T b)[0:nP] was written by the owner of b
+      phase(PH_ITRSV);
       if (!trsv(nP)) return false;
+      phase(PH_INNER);
     }
   }
 
@@ -948,23 +953,42 @@ struct Engine {
   __device__ bool delete_position(int q) {
     const int np = nP;
     const int nrot = np - 1 - q;
-    flops(PH_INNER, 3.0 * (double)nrot * (nrot + 1) + 6.0 * (double)nrot * (double)(I.n - np + 2));
+    flops(PH_CHAIN, 3.0 * (double)nrot * (nrot + 1));
+    flops(PH_ZROT, 6.0 * (double)nrot * (double)(I.n - np + 2));
     if (tm.rank == 0) {
       // the removed column re-enters Z in trailing form: W(:, c) = [R(0:q, slot); 0]
       const int c = ldcg(I.order + q);
       const int sq = ldcg(I.rslot + q);
       double* wc = Wcol(c);
       for (int i = tid; i < I.m; i += NT) wc[i] = (i <= q) ? ldcg(Rcol(sq) + i) : 0.0;
-      __syncthreads();
+      // shift positions q+1..np-1 down by one (read all, then write all)
+      const int cnt = np - 1 - q;
+      constexpr int PER = 8;  // positions per thread per sweep
+      for (int base = 0; base < cnt; base += NT * PER) {
+        int oc[PER], sl[PER];
+        double xv[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int p = q + base + tid + k * NT;
+          oc[k] = (p < np - 1) ? ldcg(I.order + p + 1) : -1;
+          sl[k] = (p < np - 1) ? ldcg(I.rslot + p + 1) : 0;
+          xv[k] = (p < np - 1) ? ldcg(I.xP + p + 1) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int p = q + base + tid + k * NT;
+          if (p < np - 1) {
+            I.order[p] = oc[k];
+            I.rslot[p] = sl[k];
+            I.xP[p] = xv[k];
+            I.pos[oc[k]] = p;
+          }
+        }
+        __syncthreads();
+      }
       if (tid == 0) {
         I.pos[c] = -1;
-        for (int p = q; p < np - 1; ++p) {
-          const int oc = ldcg(I.order + p + 1);
-          I.rslot[p] = ldcg(I.rslot + p + 1);
-          I.order[p] = oc;
-          I.xP[p] = ldcg(I.xP + p + 1);
-          I.pos[oc] = p;
-        }
         I.rslot[np - 1] = sq;
         I.order[np - 1] = -1;
         I.xP[np - 1] = 0.0;
@@ -972,6 +996,7 @@ struct Engine {
       }
     }
     if (!sync()) return false;
+    phase(PH_CHAIN);
     // (i) rotation chain on R.  Block b covers generating positions
     // [q + b*DB, q + (b+1)*DB); lane l of warp 0 owns position bs + l.
     const int nblk = (nrot + DB - 1) / DB;
@@ -1069,6 +1094,7 @@ struct Engine {
       }
     }
     if (!sync()) return false;
+    phase(PH_ZROT);
     nP = np - 1;
     // (ii) the same rotations on every Z column and on b: one warp per
     // column; the carry recurrence c' = -s c + cs * bot is affine, so each
@@ -1131,7 +1157,9 @@ struct Engine {
         for (int p = tid; p < nP; p += NT) I.rhs[p] = ldcg(I.bt + p);
       }
     }
-    return sync();
+    const bool ok = sync();
+    phase(PH_INNER);
+    return ok;
   }
 
   __device__ int* tm_err();
@@ -1318,8 +1346,9 @@ struct Engine {
         rank_limited = 1;
         break;
       }
-      phase(PH_SOLVE);
+      phase(PH_FEAS);
       if (!feasibility()) return fail_out();
+      phase(PH_SOLVE);
       // y_P: rhs = (Q^T b)[0:nP] - R12 y_J, then back substitution
       {
         __shared__ double s_yj[KM];

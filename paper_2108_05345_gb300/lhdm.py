@@ -24,7 +24,8 @@ LHDM_ERR_TIMEOUT = 6
 LHDM_ERR_ALLOC = 7
 LHDM_ERR_NO_STATE = 8
 KMAX_LIMIT = 64
-PHASES = ("setup", "dm", "panel", "solve", "commit", "inner", "residual", "dual")
+PHASES = ("setup", "dm", "panel", "solve", "commit", "inner", "residual", "dual",
+          "feasibility", "chain", "zrot", "inner_trsv")
 
 
 class Params(C.Structure):
