@@ -48,6 +48,8 @@ extern "C" {
 #define LHDM_ERR_TIMEOUT 6     /* a device-side wait exceeded its bound      */
 #define LHDM_ERR_ALLOC 7       /* device or host allocation failed           */
 #define LHDM_ERR_NO_STATE 8    /* backward called without a matching solve   */
+#define LHDM_ERR_TOO_LARGE 9   /* beyond the fixed workspace of the
+                                  allocation-free entry point              */
 
 /* Largest supported block size k_max (columns chosen per outer step). */
 #define LHDM_KMAX_LIMIT 64
@@ -143,6 +145,40 @@ int lhdm_solve(lhdm_ctx* ctx, int32_t m, int32_t n, const double* A, int32_t lda
 int lhdm_solve_host(lhdm_ctx* ctx, int32_t m, int32_t n, const double* A, int32_t lda,
                     const double* b, const lhdm_params* prm, double* x, int32_t* passive,
                     lhdm_info* info, void* stream);
+
+/*
+ * lhdm_solve_noalloc: the single solve of lhdm_solve for callers that must
+ * not allocate device memory -- code running where cudaMalloc is not
+ * allowed or not wanted (a real-time or embedded loop with a fixed memory
+ * budget, a plug-in inside a host framework that owns the device heap, a
+ * recovery path entered after an allocation failed).  It takes no context:
+ * all workspace is one statically sized device array compiled into the
+ * library, so this call allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine).
+ *
+ * The paper has no counterpart: it is a deployment variant of the same
+ * kernel, with the same arithmetic and results as lhdm_solve.
+ *
+ * Limits: m <= 256 and n <= 512 (larger sizes return LHDM_ERR_TOO_LARGE
+ * without launching anything), on a GPU with at most 160 SMs.  The array
+ * (5 MiB) occupies device memory on every GPU that loads the library until
+ * the process exits.
+ *
+ * Arguments as lhdm_solve, except:
+ *  info   DEVICE pointer to one lhdm_info the call writes (required).
+ * The call is asynchronous on `stream`.  The first call on each device
+ * looks up the array's device address and sets kernel attributes, so make
+ * that first call before capturing a stream.  Every call shares the one
+ * array and overwrites it (the kernel re-initialises all the state it
+ * reads; the barrier words are cleared with cudaMemsetAsync): calls whose
+ * work overlaps on the GPU -- concurrent streams, or several host threads
+ * -- race and corrupt each other, so serialise them (one stream is enough).
+ * No adjoint state is kept for lhdm_backward.
+ * Errors: INVALID_ARG, TOO_LARGE, CUDA.
+ */
+int lhdm_solve_noalloc(int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
+                       const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info,
+                       void* stream);
 
 /* Copies the report of the last solve on ctx to *info (host); synchronises. */
 int lhdm_get_info(lhdm_ctx* ctx, lhdm_info* info, void* stream);

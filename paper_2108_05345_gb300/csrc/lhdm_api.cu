@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -326,6 +327,7 @@ const char* lhdm_status_string(int s) {
     case LHDM_ERR_TIMEOUT: return "a bounded device-side wait expired";
     case LHDM_ERR_ALLOC: return "allocation failed";
     case LHDM_ERR_NO_STATE: return "no solve state for the adjoint";
+    case LHDM_ERR_TOO_LARGE: return "problem larger than the static workspace of lhdm_solve_noalloc";
     default: return "unknown status";
   }
 }
@@ -570,6 +572,123 @@ int lhdm_backward(lhdm_ctx* c, const double* A, int32_t lda, const double* dLdx,
   void* args[] = {(void*)&I, (void*)&c->bar, (void*)&c->err, (void*)&dLdx, (void*)&dLdb,
                   (void*)&dLdA, (void*)&ld_dA, (void*)&apu_arg};
   e = cudaLaunchCooperativeKernel((const void*)lhdm_backward_grid_kernel, dim3(c->nsm), dim3(NT), args, DYN_SMEM, st);
+  return cuda_ok(e);
+}
+
+
+// ----------------------------------------------------------------------- allocation-free solve
+// Callers that cannot allocate device memory (see lhdm_solve_noalloc) use one
+// workspace that lives in a file-scope device array for the life of the
+// process: its address is taken once per device, every call reuses it.
+constexpr int NOALLOC_MAX_M = 256;
+constexpr int NOALLOC_MAX_N = 512;
+constexpr int NOALLOC_MAX_TEAM = 160;                // SMs the workspace is sized for
+constexpr size_t NOALLOC_WORDS = (size_t)640 * 1024;  // 8-byte words: 5 MiB
+static __device__ __align__(256) double g_lhdm_noalloc_scratch[NOALLOC_WORDS];
+
+struct NoallocDevice {
+  bool ready = false;
+  int nsm = 0;
+  double* base = nullptr;  // device address of g_lhdm_noalloc_scratch
+  ScratchLayout L{};
+  int cap = 0, ldr = 0;
+  size_t oR = 0, oxP = 0, oR2 = 0, oI = 0;  // word offsets
+};
+static std::mutex g_noalloc_mu;
+static NoallocDevice g_noalloc[64];
+
+// Per-device set-up (first call on the device, with it current): the symbol's
+// device address, kernel attributes and the fixed workspace layout.
+static int noalloc_setup(NoallocDevice& d) {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_lhdm_noalloc_scratch) != cudaSuccess || !ptr) return LHDM_ERR_CUDA;
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LHDM_ERR_CUDA;
+  int rc = set_attrs();
+  if (rc) return rc;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lhdm_solve_grid_kernel, NT, DYN_SMEM) != cudaSuccess ||
+      occ < 1)
+    return LHDM_ERR_CUDA;
+  if (nsm > NOALLOC_MAX_TEAM) return LHDM_ERR_TOO_LARGE;
+  d.nsm = nsm;
+  d.base = static_cast<double*>(ptr);
+  d.L = make_layout(NOALLOC_MAX_M, NOALLOC_MAX_N, nsm);
+  d.cap = std::min(NOALLOC_MAX_M, NOALLOC_MAX_N);
+  d.ldr = (d.cap + 1) & ~1;
+  size_t o = d.L.dtotal;
+  d.oR = o;
+  o += up8((size_t)d.ldr * d.cap);
+  d.oxP = o;
+  o += up8(d.cap);
+  d.oR2 = o;  // residual r
+  o += up8(NOALLOC_MAX_M);
+  d.oI = o;   // int region: scratch ints, rslot, order, nP, barrier words, error flag
+  const size_t ints = d.L.itotal + 2 * up8(d.cap) + 3 * 32;
+  o += (ints + 1) / 2;
+  if (o > NOALLOC_WORDS) return LHDM_ERR_TOO_LARGE;
+  d.ready = true;
+  return LHDM_OK;
+}
+
+extern "C" int lhdm_solve_noalloc(int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
+                                  const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info,
+                                  void* stream) {
+  if (m < 0 || n < 0 || lda < std::max(1, m) || !info) return LHDM_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && !A) || (m > 0 && !b) || (n > 0 && (!x || !passive))) return LHDM_ERR_INVALID_ARG;
+  if (m > NOALLOC_MAX_M || n > NOALLOC_MAX_N) return LHDM_ERR_TOO_LARGE;
+  lhdm_params p;
+  lhdm_default_params(&p);
+  if (prm) p = *prm;
+  int rc = check_params(&p, false);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LHDM_ERR_CUDA;
+  NoallocDevice* d = &g_noalloc[dev];
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!d->ready) {
+      rc = noalloc_setup(*d);
+      if (rc) return rc;
+    }
+  }
+  double* base = d->base;
+  int* ib = reinterpret_cast<int*>(base + d->oI);
+  Inst I;
+  std::memset(&I, 0, sizeof(I));
+  bind_scratch(I, d->L, base, ib);
+  I.m = m;
+  I.n = n;
+  I.lda = lda;
+  I.A = A;
+  I.b = b;
+  I.x_out = x;
+  I.passive_out = passive;
+  I.info_out = info;
+  I.cap = std::min(m, n);
+  I.ldr = d->ldr;
+  I.R = base + d->oR;
+  I.xP = base + d->oxP;
+  I.r = base + d->oR2;
+  int* tail = ib + d->L.itotal;
+  I.rslot = tail;
+  I.order = tail + up8(d->cap);
+  I.nP_out = tail + 2 * up8(d->cap);
+  unsigned int* bar = reinterpret_cast<unsigned int*>(tail + 2 * up8(d->cap) + 32);
+  int* err = tail + 2 * up8(d->cap) + 64;
+  I.phase_ns = nullptr;
+  I.trace = nullptr;
+  I.trace_cap = 0;
+  I.prm = to_dev(p);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the barrier words and the error flag must start at zero; everything
+  // else is (re)initialised by the kernel itself
+  cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  void* args[] = {(void*)&I, (void*)&bar, (void*)&err};
+  e = cudaLaunchCooperativeKernel((const void*)lhdm_solve_grid_kernel, dim3(d->nsm), dim3(NT), args, DYN_SMEM, st);
   return cuda_ok(e);
 }
 

@@ -23,6 +23,7 @@ LHDM_ERR_CUDA = 5
 LHDM_ERR_TIMEOUT = 6
 LHDM_ERR_ALLOC = 7
 LHDM_ERR_NO_STATE = 8
+LHDM_ERR_TOO_LARGE = 9
 KMAX_LIMIT = 64
 PHASES = ("setup", "dm", "panel", "solve", "commit", "inner", "residual", "dual",
           "feasibility", "chain", "zrot", "inner_trsv")
@@ -66,6 +67,7 @@ def lib():
         L.lhdm_destroy.argtypes = [V]
         L.lhdm_solve.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
         L.lhdm_solve_host.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
+        L.lhdm_solve_noalloc.argtypes = [i32, i32, d, i32, d, P, d, d, d, V]
         L.lhdm_get_info.argtypes = [V, I, V]
         L.lhdm_backward.argtypes = [V, d, i32, d, d, d, i32, V]
         L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
@@ -123,6 +125,33 @@ def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+def solve_noalloc(A, b, params=None, x=None, passive=None, info=None, stream=None):
+    """lhdm_solve_noalloc: the solve without any device allocation inside
+    the library (fixed static workspace; m <= 256, n <= 512).  x, passive
+    and info (a device buffer of one lhdm_info, as 6 float64) may be given
+    by the caller; returns the raw status code and the three tensors."""
+    m, n = A.shape
+    lda = _lda(A)
+    dev = A.device
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+    if passive is None:
+        passive = torch.empty(n, dtype=torch.int32, device=dev)
+    if info is None:
+        info = torch.zeros(C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
+    rc = lib().lhdm_solve_noalloc(m, n, A.data_ptr() if A.numel() else None, lda,
+                                  b.data_ptr() if b.numel() else None,
+                                  C.byref(params) if params is not None else None,
+                                  x.data_ptr() if n else None, passive.data_ptr() if n else None,
+                                  info.data_ptr(), _stream(stream))
+    return rc, x, passive, info
+
+
+def info_from_device(buf):
+    """An lhdm_info held in a device float64 buffer -> dict."""
+    return Info.from_buffer_copy(buf.cpu().numpy().tobytes()).as_dict()
 
 
 class Context:
