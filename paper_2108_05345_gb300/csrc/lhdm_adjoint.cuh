@@ -6,8 +6,8 @@
 // g = dL/dx, u = (R^T R)^{-1} g_P and r = b - A x:
 //   dL/db   = A_P u
 //   dL/dA_P = r u^T - (A_P u) x_P^T,   dL/dA_Z = 0.
-// R^T v = g_P is a forward substitution, R u = v the back substitution of
-// the solve; both reuse the blocked scheme of Engine::trsv.
+// R^T v = g_P is a blocked forward substitution, R u = v the back
+// substitution of the solve (Engine::trsv).
 #pragma once
 
 #include "lhdm_solve.cuh"
@@ -94,6 +94,7 @@ struct Adjoint {
       for (int p = gt; p < np; p += nt) I.rhs[p] = __ldg(g + ldcg(I.order + p));
       for (int c = gt; c < I.n; c += nt) I.pos[c] = -1;
     }
+    E.clear_tri_flags();
     if (!E.sync()) return false;
     {
       const int gt = E.tm.rank * NT + tid, nt = E.tm.size * NT;

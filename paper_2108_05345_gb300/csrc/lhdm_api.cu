@@ -59,10 +59,12 @@ struct BatchItem {
 // Offsets of one team's scratch inside a double region and an int region.
 struct ScratchLayout {
   size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, candw, rotc, rots, apu;
+  size_t Dinv, accb;  // pipelined triangular solve (teams of more than one CTA)
   size_t dtotal;
-  size_t pos, J, candi, candn, ipart, ctl, qlist;
+  size_t pos, J, candi, candn, ipart, ctl, qlist, tflag;
   size_t itotal;
   int ldw;
+  bool pipelined;
 };
 
 static size_t up8(size_t x) { return (x + 31) & ~(size_t)31; }  // 256-byte granules of doubles/ints
@@ -94,6 +96,11 @@ static ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.rotc = take(cap);
   L.rots = take(cap);
   L.apu = take(m);
+  // diagonal-block inverses and slab accumulators of the pipelined solve
+  const size_t nbk = (size_t)(cap + TB - 1) / TB;
+  L.pipelined = team > 1;
+  L.Dinv = take(L.pipelined ? nbk * TB * TB : 1);
+  L.accb = take(L.pipelined ? nbk * TB : 1);
   L.dtotal = o;
   o = 0;
   L.pos = take(n);
@@ -103,6 +110,7 @@ static ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.ipart = take((size_t)team * 8);
   L.ctl = take(16);
   L.qlist = take(cap);
+  L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB) : 1);
   L.itotal = o;
   return L;
 }
@@ -135,6 +143,9 @@ static __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.ipart = ip + L.ipart;
   I.ctl = ip + L.ctl;
   I.qlist = ip + L.qlist;
+  I.Dinv = L.pipelined ? d + L.Dinv : nullptr;
+  I.accb = L.pipelined ? d + L.accb : nullptr;
+  I.tflag = L.pipelined ? ip + L.tflag : nullptr;
   I.amask = nullptr;
 }
 

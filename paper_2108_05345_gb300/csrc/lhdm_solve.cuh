@@ -38,6 +38,8 @@ struct Engine {
   bool u_dirty = false;
   bool failed = false;
   int kdm = 0, removed = 0, inner_step = 0;
+  int inv_valid = 0;  // positions whose diagonal-block inverse column is current
+  int tepoch = 0;     // pipelined-solve calls in this launch (flag values)
 
   // phase timing (rank 0, thread 0)
   long long t_last = 0;
@@ -78,6 +80,14 @@ struct Engine {
 
   __device__ __forceinline__ double* Rcol(int slot) const { return I.R + (size_t)slot * I.ldr; }
   __device__ __forceinline__ double* Wcol(int c) const { return I.W + (size_t)c * I.ldw; }
+
+  // Flags of the pipelined solve start at zero in every launch (a barrier
+  // must follow before the first solve).
+  __device__ void clear_tri_flags() {
+    if (!I.tflag) return;
+    const int nbk = (I.cap + TB - 1) / TB, nfl = nbk * (1 + TB / SLAB);
+    for (int i = tm.rank * NT + tid; i < nfl; i += tm.size * NT) I.tflag[i] = 0;
+  }
 
   // ------------------------------------------------------------ setup
   // Algorithm 3, first lines: x = 0, w = A^T b, u = column norms of A; W = A.
@@ -130,6 +140,7 @@ struct Engine {
       I.order[p] = -1;
     }
     if (tm.rank == 0 && tid < 16) I.ctl[tid] = 0;
+    clear_tri_flags();
     am = block_max(am, sh);
     bs = block_sum(bs, sh);
     bad = block_sum_int(bad, shi);
@@ -605,14 +616,21 @@ struct Engine {
   }
 
   // ------------------------------------------------------------ triangular solve
-  // R y = rhs for positions [0, np) (blocked back substitution, one barrier
-  // per TB-block).  Rank 0 solves each diagonal block from shared memory
-  // (staged in parallel) after folding in the block just solved; the other
-  // rows receive that block's contribution spread over the whole team.
-  // rhs is consumed.
+  // R y = rhs on positions [0, np) (the back substitution of subproblem (6));
+  // y lands in yP.  Teams of several CTAs with more than two TB-blocks take
+  // the flag-pipelined solve, everything else the blocked solve.
   __device__ bool trsv(int np) {
     if (np <= 0) return true;
     flops(cur_phase < 0 ? PH_SOLVE : cur_phase, (double)np * np);
+    if (I.Dinv && tm.size >= 2 && np > 2 * TB) return trsv_pipelined(np);
+    return trsv_blocked(np);
+  }
+
+  // Blocked back substitution, one team barrier per TB-block.  Rank 0 solves
+  // each diagonal block from shared memory (staged in parallel) after folding
+  // in the block just solved; the other rows receive that block's
+  // contribution spread over the whole team.  rhs is consumed.
+  __device__ bool trsv_blocked(int np) {
     const int nb = (np + TB - 1) / TB;
     __shared__ double s_y[TB];
     __shared__ int s_slot[TB];
@@ -705,6 +723,270 @@ struct Engine {
       if (!sync()) return false;
     }
     return true;
+  }
+
+
+  // Flag-pipelined back substitution (teams of several CTAs).  Positions are
+  // cut into TB-blocks; rank 0 walks them from the last to the first and is
+  // the only CTA on the dependency chain.  For block b with right-hand side
+  // a_b = rhs_b - R(b, b+1) y_{b+1} - acc_b it forms y_b = D_b^{-1} a_b with
+  // the inverse of the diagonal block D_b kept from earlier solves, and back
+  // substitution for the columns whose inverse is stale.  acc_b, the blocks
+  // b+2, b+3, ... of the row block, is accumulated by ranks 1, 2, ... in
+  // SLAB-row slabs as soon as each y block is published (a flag per block)
+  // and handed back through a flag per slab.  The last ranks compute the
+  // stale inverse columns meanwhile, for the solves that follow.  Column j of
+  // the inverse of an upper triangular block depends only on the block's
+  // leading (j+1) x (j+1) part, so appending positions leaves every computed
+  // column valid; a deletion at position q invalidates positions >= q.
+  __device__ bool trsv_pipelined(int np) {
+    const int nb = (np + TB - 1) / TB;
+    const int ep = ++tepoch;
+    bool ok = true;
+    if (tm.rank == 0) {
+      ok = tri_chain(np, nb, ep);
+    } else {
+      ok = tri_slabs(np, nb, ep);
+      if (ok) tri_inverse(np, nb);
+    }
+    if (!ok) {
+      failed = true;
+      status = LHDM_ERR_TIMEOUT;
+      return false;
+    }
+    if (!sync()) return false;
+    inv_valid = np;
+    return true;
+  }
+
+  __device__ __forceinline__ int* yflags() const { return I.tflag; }
+  __device__ __forceinline__ int* sflags() const { return I.tflag + (I.cap + TB - 1) / TB; }
+
+  // Rank 0: the chain over the blocks (see trsv_pipelined).
+  __device__ bool tri_chain(int np, int nb, int ep) {
+    double* sD = dyn;                       // TB x (TB+1) stale diagonal columns
+    double* sP = dyn + TB * (TB + 1);       // 8 x TB partial sums
+    __shared__ double s_a[TB];
+    __shared__ double s_y[2][TB];
+    __shared__ double s_rinv[TB];
+    __shared__ int s_bslot[TB], s_cslot[TB];
+    const int row = tid & (TB - 1), g = tid >> 6;  // 8 groups of 8 columns
+    int* yfl = yflags();
+    const int* sfl = sflags();
+    for (int bi = nb - 1; bi >= 0; --bi) {
+      const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
+      const int c0 = b0 + TB, nc = (bi + 1 < nb) ? min(np, c0 + TB) - c0 : 0;
+      const int v = min(max(inv_valid - b0, 0), nbk);  // columns with a valid inverse
+      double* ycur = s_y[bi & 1];
+      const double* ynext = s_y[(bi + 1) & 1];
+      if (tid < nbk) s_bslot[tid] = ldcg(I.rslot + b0 + tid);
+      if (tid >= TB && tid - TB < nc) s_cslot[tid - TB] = ldcg(I.rslot + c0 + tid - TB);
+      __syncthreads();
+      // loads that do not wait for y: tile R(b, b+1), inverse columns, rhs,
+      // stale columns of the diagonal block
+      double rt[8], di[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = g * 8 + q;
+        rt[q] = (row < nbk && j < nc) ? ldcg(Rcol(s_cslot[j]) + b0 + row) : 0.0;
+        di[q] = (row <= j && j < v) ? ldcg(I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB + row) : 0.0;
+      }
+      const double rh = (g == 0 && row < nbk) ? ldcg(I.rhs + b0 + row) : 0.0;
+      if (v < nbk) {
+        const int ns = (nbk - v) * TB;  // <= TB * TB = 8 per thread
+        double sv[TB * TB / NT];
+#pragma unroll
+        for (int k = 0; k < TB * TB / NT; ++k) {
+          const int idx = tid + k * NT, j = v + idx / TB, i = idx & (TB - 1);
+          sv[k] = (idx < ns && i <= j) ? ldcg(Rcol(s_bslot[j]) + b0 + i) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < TB * TB / NT; ++k) {
+          const int idx = tid + k * NT, j = v + idx / TB, i = idx & (TB - 1);
+          if (idx < ns) {
+            sD[j * (TB + 1) + i] = sv[k];
+            if (i == j) s_rinv[j] = 1.0 / sv[k];
+          }
+        }
+      }
+      // contribution of block b+1 (just solved) to this block's rows
+      if (nc > 0) {
+        double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          p0 = fma(rt[q], ynext[g * 8 + q], p0);
+          p1 = fma(rt[q + 1], ynext[g * 8 + q + 1], p1);
+        }
+        sP[g * TB + row] = p0 + p1;
+      }
+      // slab accumulations of blocks b+2, ...
+      int okw = 1;
+      double acc = 0.0;
+      if (g == 0 && row < nbk && bi + 2 < nb) {
+        okw = wait_ge(sfl + (b0 + row) / SLAB, ep, tm_err()) ? 1 : 0;
+        if (okw) acc = ldcg(I.accb + b0 + row);
+      }
+      if (!__syncthreads_and(okw)) return false;
+      if (g == 0 && row < nbk) {
+        double a = rh - acc;
+        if (nc > 0) {
+          const double s01 = sP[row] + sP[TB + row], s23 = sP[2 * TB + row] + sP[3 * TB + row];
+          const double s45 = sP[4 * TB + row] + sP[5 * TB + row], s67 = sP[6 * TB + row] + sP[7 * TB + row];
+          a -= (s01 + s23) + (s45 + s67);
+        }
+        s_a[row] = a;
+      }
+      __syncthreads();
+      if (v < nbk) {
+        // back substitution over the stale columns [v, nbk); the rows
+        // above v receive their contributions on the way
+        if (warp == 0) {
+          double a0 = (lane < nbk) ? s_a[lane] : 0.0;
+          double a1 = (lane + 32 < nbk) ? s_a[lane + 32] : 0.0;
+          for (int l = nbk - 1; l >= v; --l) {
+            const int own = l & 31;
+            const double* cl = sD + l * (TB + 1);
+            double yv = (l >= 32 ? a1 : a0) * s_rinv[l];
+            yv = __shfl_sync(0xffffffffu, yv, own);
+            if (lane == own) ycur[l] = yv;
+            if (lane < l) a0 = fma(-cl[lane], yv, a0);
+            if (lane + 32 < l) a1 = fma(-cl[lane + 32], yv, a1);
+          }
+          if (lane < v) s_a[lane] = a0;
+          if (lane + 32 < v) s_a[lane + 32] = a1;
+        }
+        __syncthreads();
+      }
+      if (v > 0) {
+        // y = D^{-1} a on the columns with a valid inverse (upper triangle:
+        // warps whose rows all lie below their columns skip)
+        double p0 = 0.0, p1 = 0.0;
+        if (g * 8 + 7 >= (row & 32)) {
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            const int j = g * 8 + q;
+            if (j < v) p0 = fma(di[q], s_a[j], p0);
+            if (j + 1 < v) p1 = fma(di[q + 1], s_a[j + 1], p1);
+          }
+        }
+        sP[g * TB + row] = p0 + p1;
+        __syncthreads();
+        if (g == 0 && row < v) {
+          const double s01 = sP[row] + sP[TB + row], s23 = sP[2 * TB + row] + sP[3 * TB + row];
+          const double s45 = sP[4 * TB + row] + sP[5 * TB + row], s67 = sP[6 * TB + row] + sP[7 * TB + row];
+          ycur[row] = (s01 + s23) + (s45 + s67);
+        }
+      }
+      if (g == 0 && row < nbk) {
+        I.yP[b0 + row] = ycur[row];
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) atomicExch(yfl + bi, ep);
+    }
+    return true;
+  }
+
+  // Ranks >= 1: slab s (rows [SLAB s, SLAB s + SLAB), row block s / (TB/SLAB))
+  // on rank 1 + s mod (size-1), largest s first.  Sums R(slab, c) y_c over
+  // c = nb-1 down to row block + 2 as the blocks are published, then hands
+  // the sum to rank 0.  Thread = (row, column pair); the R loads of a block
+  // are issued before its flag is awaited.
+  __device__ bool tri_slabs(int np, int nb, int ep) {
+    constexpr int SPB = TB / SLAB;        // slabs per block
+    const int nslab = SPB * (nb - 2);
+    const int nh = tm.size - 1, h = tm.rank - 1;
+    if (h >= nslab) return true;
+    double* s_red = dyn;                  // (NT / SLAB) x SLAB
+    const int row = tid & (SLAB - 1), cg = tid / SLAB;   // cg in [0, 32)
+    const int* yfl = yflags();
+    int* sfl = sflags();
+    for (int s = h + nh * ((nslab - 1 - h) / nh); s >= 0; s -= nh) {
+      const int rb = s / SPB, r0 = s * SLAB;
+      double acc = 0.0;
+      for (int c = nb - 1; c >= rb + 2; --c) {
+        const int c0 = c * TB, nc = min(np, c0 + TB) - c0;
+        const int j0 = cg, j1 = cg + 32;
+        const int sl0 = (j0 < nc) ? ldcg(I.rslot + c0 + j0) : 0;
+        const int sl1 = (j1 < nc) ? ldcg(I.rslot + c0 + j1) : 0;
+        const double v0 = (j0 < nc) ? ldcg(Rcol(sl0) + r0 + row) : 0.0;
+        const double v1 = (j1 < nc) ? ldcg(Rcol(sl1) + r0 + row) : 0.0;
+        int okw = 1;
+        if (tid == 0) okw = wait_ge(yfl + c, ep, tm_err()) ? 1 : 0;
+        if (!__syncthreads_and(okw)) return false;
+        const double y0 = (j0 < nc) ? ldcg(I.yP + c0 + j0) : 0.0;
+        const double y1 = (j1 < nc) ? ldcg(I.yP + c0 + j1) : 0.0;
+        acc = fma(v0, y0, acc);
+        acc = fma(v1, y1, acc);
+      }
+      s_red[cg * SLAB + row] = acc;
+      __syncthreads();
+      if (warp < SLAB) {
+        const double t = warp_sum(s_red[lane * SLAB + warp]);
+        if (lane == 0) {
+          I.accb[r0 + warp] = t;
+          __threadfence();
+        }
+      }
+      __syncthreads();
+      if (tid == 0) atomicExch(sfl + s, ep);
+    }
+    return true;
+  }
+
+  // Last ranks: inverse columns of the diagonal blocks for the positions
+  // [inv_valid, np).  Item k = (block, column class mod 4) on rank
+  // size-1 - k mod (size-1); one warp per column, which solves D x = e_j by
+  // column-oriented substitution and writes column j of D^{-1} (zeros below
+  // the diagonal).
+  __device__ void tri_inverse(int np, int nb) {
+    constexpr int PARTS = TB / NW;        // 4 column classes, one column per warp
+    const int bs = inv_valid / TB;
+    const int nitem = PARTS * (nb - bs);
+    const int nh = tm.size - 1, h = tm.size - 1 - tm.rank;
+    if (nitem <= 0 || h >= nitem) return;
+    double* sD = dyn;
+    __shared__ double s_ri[TB];
+    for (int it = h; it < nitem; it += nh) {
+      const int bi = bs + it / PARTS, part = it % PARTS;
+      const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
+      const int v = min(max(inv_valid - b0, 0), nbk);
+      __syncthreads();  // the previous item's readers of sD are done
+      {
+        double sv[TB * TB / NT];
+#pragma unroll
+        for (int k = 0; k < TB * TB / NT; ++k) {
+          const int idx = tid + k * NT, j = idx / TB, i = idx & (TB - 1);
+          sv[k] = (j < nbk && i <= j) ? ldcg(Rcol(ldcg(I.rslot + b0 + j)) + b0 + i) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < TB * TB / NT; ++k) {
+          const int idx = tid + k * NT, j = idx / TB, i = idx & (TB - 1);
+          sD[j * (TB + 1) + i] = sv[k];
+          if (i == j && j < nbk) s_ri[j] = 1.0 / sv[k];
+        }
+      }
+      __syncthreads();
+      const int j = part + PARTS * warp;
+      if (j >= v && j < nbk) {
+        double a0 = (lane == j) ? 1.0 : 0.0;
+        double a1 = (lane + 32 == j) ? 1.0 : 0.0;
+        for (int l = j; l >= 0; --l) {
+          const int own = l & 31;
+          const double* cl = sD + l * (TB + 1);
+          double xv = (l >= 32 ? a1 : a0) * s_ri[l];
+          xv = __shfl_sync(0xffffffffu, xv, own);
+          if (lane == own) {
+            if (l >= 32) a1 = xv; else a0 = xv;
+          }
+          if (lane < l) a0 = fma(-cl[lane], xv, a0);
+          if (lane + 32 < l) a1 = fma(-cl[lane + 32], xv, a1);
+        }
+        double* out = I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB;
+        out[lane] = (lane <= j) ? a0 : 0.0;
+        out[lane + 32] = (lane + 32 <= j) ? a1 : 0.0;
+      }
+    }
   }
 
   // ------------------------------------------------------------ commit
@@ -952,6 +1234,7 @@ struct Engine {
   // counter), then the same rotations applied to every Z column and to b.
   __device__ bool delete_position(int q) {
     const int np = nP;
+    inv_valid = min(inv_valid, q);
     const int nrot = np - 1 - q;
     flops(PH_CHAIN, 3.0 * (double)nrot * (nrot + 1));
     flops(PH_ZROT, 6.0 * (double)nrot * (double)(I.n - np + 2));
