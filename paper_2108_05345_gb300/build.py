@@ -1,19 +1,22 @@
 """Builds the CUDA library liblhdm.so in-tree for sm_103a (GB300) with nvcc.
 
-One translation unit (csrc/lhdm_api.cu plus its headers); the result sits
+Four translation units (the host side of the C ABI and one per kernel
+family) compile in parallel and link into one shared library, which sits
 next to this file and is what paper_2108_05345_gb300.lhdm loads.
 """
 import os
 import subprocess
 import sys
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "liblhdm.so")
-SOURCES = ["lhdm_api.cu"]
-HEADERS = ["lhdm_engine.cuh", "lhdm_solve.cuh", "lhdm_adjoint.cuh"]
+SOURCES = ["lhdm_api.cu", "lhdm_grid_solve.cu", "lhdm_batch_solve.cu", "lhdm_backward.cu"]
+HEADERS = ["lhdm_engine.cuh", "lhdm_solve.cuh", "lhdm_adjoint.cuh", "lhdm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def _stale():
@@ -28,14 +31,23 @@ def build(force=False, verbose=False):
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    inc = ["-I", os.path.join(ROOT, "include")]
+    with tempfile.TemporaryDirectory(prefix="lhdm_build_") as tmpdir:
+        objs, procs = [], []
+        for src in SOURCES:
+            obj = os.path.join(tmpdir, os.path.splitext(src)[0] + ".o")
+            cmd = [nvcc, *ARCH, *FLAGS, *inc, "-c", os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+                print(" ".join(cmd))
+            procs.append((cmd, subprocess.Popen(cmd)))
+            objs.append(obj)
+        failed = [cmd for cmd, p in procs if p.wait() != 0]
+        if failed:
+            raise subprocess.CalledProcessError(1, failed[0])
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+        os.replace(tmp, LIB)
     return LIB
 
 

@@ -7,7 +7,7 @@
 namespace lhdm {
 
 // Dynamic shared memory per CTA (bytes) used by the phases below.
-constexpr int DYN_SMEM = 64 * 1024;
+constexpr int DYN_SMEM = 160 * 1024;
 constexpr int CAND_LOCAL_MAX = 2048;     // local DM candidates per CTA
 constexpr int CAND_STAGE = 4096;         // merged candidates staged per pass
 constexpr int ROT_STAGE = 2048;          // rotations staged per pass
@@ -989,6 +989,182 @@ struct Engine {
     }
   }
 
+
+  // Shared-memory layout and chunk sizes of one commit (see commit()).
+  struct CommitShape {
+    int L, RC1, RC2, VS;
+    double* wk;        // work area
+    double* s_D;       // KM x CB
+    double* s_E;       // KM x CB
+    const double* s_T; // packed T^T rows
+    const double* s_vt;
+    double* s_nrm;     // NW x CB
+    const int* s_cid;  // batch columns (-1: b)
+  };
+  static constexpr int CB = 16;  // Z columns per commit batch
+
+  __device__ __forceinline__ double* commit_col(const int* s_cid, int k) const {
+    const int id = s_cid[k];
+    return (id >= 0 ? Wcol(id) : I.bt) + nP;
+  }
+
+  // Rows [rb, rb+nr) of V (kp columns) into wk with row stride VS.
+  __device__ __forceinline__ void stage_vrows(const CommitShape& cs, int rb, int nr) {
+    const int tot = nr * kp;
+    for (int e0 = tid; e0 < tot; e0 += 4 * NT) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + k * NT, rr = e / kp, t = e - rr * kp, rg = rb + rr;
+        v[k] = (e < tot && rg > t) ? ldcg(I.V + (size_t)rg * KM + t) : ((e < tot && rg == t) ? cs.s_vt[t] : 0.0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + k * NT, rr = e / kp, t = e - rr * kp;
+        if (e < tot) cs.wk[rr * cs.VS + t] = v[k];
+      }
+    }
+  }
+
+  // One batch of NB columns: D = V^T C (pass 1: thread (t1, g1) sums rows
+  // g1, g1+G, ... of every chunk, then a fixed pairwise tree over g1),
+  // D' = T^T D, C -= V D' and the trailing norms (pass 2: thread (r2, grp)
+  // updates row r2 of every chunk in columns grp, grp+NG, ...).  NB is a
+  // template parameter so that no issue slot goes to absent columns.
+  template <int NB>
+  __device__ void commit_batch(const CommitShape& cs) {
+    const int L = cs.L, RC1 = cs.RC1, RC2 = cs.RC2, VS = cs.VS;
+    double* wk = cs.wk;
+    const int G = NT / kp, t1 = tid % kp, g1 = tid / kp;
+    const bool act1 = g1 < G;
+    double acc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = 0.0;
+    double* sX = wk + RC1 * VS;  // NB x RC1
+    for (int rb = 0; rb < L; rb += RC1) {
+      const int nr = min(RC1, L - rb);
+      __syncthreads();
+      stage_vrows(cs, rb, nr);
+      const int totx = NB * nr;
+      for (int e0 = tid; e0 < totx; e0 += 4 * NT) {
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = e0 + k * NT, cc = e / nr, rr = e - cc * nr;
+          v[k] = (e < totx) ? ldcg(commit_col(cs.s_cid, cc) + rb + rr) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = e0 + k * NT, cc = e / nr, rr = e - cc * nr;
+          if (e < totx) sX[cc * RC1 + rr] = v[k];
+        }
+      }
+      __syncthreads();
+      if (act1) {
+        for (int rr = g1; rr < nr; rr += G) {
+          const double v = wk[rr * VS + t1];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) acc[c] = fma(v, sX[c * RC1 + rr], acc[c]);
+        }
+      }
+    }
+    __syncthreads();
+    double* P = wk;  // G x kp x NB partials
+    if (act1) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) P[(g1 * kp + t1) * NB + c] = acc[c];
+    }
+    __syncthreads();
+    for (int st = 1; st < G; st <<= 1) {
+      if (act1 && (g1 & (2 * st - 1)) == 0 && g1 + st < G) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) P[(g1 * kp + t1) * NB + c] += P[((g1 + st) * kp + t1) * NB + c];
+      }
+      __syncthreads();
+    }
+    for (int o = tid; o < kp * NB; o += NT) {
+      const int t = o / NB, cc = o - t * NB;
+      cs.s_D[t * CB + cc] = P[t * NB + cc];
+    }
+    __syncthreads();
+    // D' = T^T D
+    for (int o = tid; o < kp * NB; o += NT) {
+      const int t = o % kp, cc = o / kp;
+      double e2 = 0.0;
+      for (int sidx = 0; sidx <= t; ++sidx) e2 = fma(cs.s_T[t * (t + 1) / 2 + sidx], cs.s_D[sidx * CB + cc], e2);
+      cs.s_E[t * CB + cc] = e2;
+    }
+    // pass 2 (NG = 1 or 2 groups of columns)
+    const int NG = NT / RC2, r2 = tid % RC2, grp = tid / RC2;
+    constexpr int NK2 = (NB + 1) / 2;
+    double nrm[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) nrm[k] = 0.0;
+    for (int rb = 0; rb < L; rb += RC2) {
+      const int nr = min(RC2, L - rb);
+      __syncthreads();
+      stage_vrows(cs, rb, nr);
+      __syncthreads();
+      if (r2 < nr) {
+        const bool below = rb + r2 >= kp;
+        if (NG == 1) {
+          double x[NB];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) x[k] = ldcg(commit_col(cs.s_cid, k) + rb + r2);
+          for (int t = 0; t < kp; ++t) {
+            const double v = wk[r2 * VS + t];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) x[k] = fma(-v, cs.s_E[t * CB + k], x[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            commit_col(cs.s_cid, k)[rb + r2] = x[k];
+            if (below) nrm[k] = fma(x[k], x[k], nrm[k]);
+          }
+        } else {
+          double x[NK2];
+#pragma unroll
+          for (int k = 0; k < NK2; ++k) {
+            const int c = grp + 2 * k;
+            x[k] = (c < NB) ? ldcg(commit_col(cs.s_cid, c) + rb + r2) : 0.0;
+          }
+          for (int t = 0; t < kp; ++t) {
+            const double v = wk[r2 * VS + t];
+#pragma unroll
+            for (int k = 0; k < NK2; ++k) {
+              const int c = grp + 2 * k;
+              if (c < NB) x[k] = fma(-v, cs.s_E[t * CB + c], x[k]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < NK2; ++k) {
+            const int c = grp + 2 * k;
+            if (c < NB) {
+              commit_col(cs.s_cid, c)[rb + r2] = x[k];
+              if (below) nrm[k] = fma(x[k], x[k], nrm[k]);
+            }
+          }
+        }
+      }
+    }
+    // norms: a group's threads are whole warps; column c = grp + NG k
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const int c = grp + NG * k;
+      if (c < NB) {
+        const double v = warp_sum(nrm[k]);
+        if (lane == 0) cs.s_nrm[warp * CB + c] = v;
+      }
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const int g = tid % NG, w0 = g * (RC2 / 32);
+      double v = 0.0;
+      for (int w2 = 0; w2 < RC2 / 32; ++w2) v += cs.s_nrm[(w0 + w2) * CB + tid];
+      if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
+    }
+  }
+
   // ------------------------------------------------------------ commit
   // Makes J[0:kp] passive: new R columns [W(0:nP, J); R22], the block
   // reflector I - V T^T V^T applied to the trailing rows of every Z column
@@ -1014,133 +1190,114 @@ struct Engine {
         I.yP[nP + tid] = ldcg(I.yJ + tid);
       }
     }
-    // (b) trailing update of this CTA's Z columns (+ b on the last CTA), in
-    // batches of CB columns: D = V^T C (pass 1), D' = T^T D, C -= V D' and
-    // the new trailing norms (pass 2).  V's triangular structure (zero above
-    // row t, v0 on row t) is folded into the staged chunks.
-    constexpr int RC = 64;  // rows per staged chunk
-    constexpr int CB = 16;  // columns per batch
-    constexpr int VS = KM + 1;          // padded row stride of the staged V chunk
-    double* s_V = dyn;                  // RC x VS
-    double* s_X = s_V + RC * VS;        // CB x RC
-    double* s_D = s_X + CB * RC;        // KM x CB
-    double* s_E = s_D + KM * CB;        // KM x CB
+    // (b) trailing update of the Z columns and of Q^T b: D = V^T C (pass 1),
+    // D' = T^T D, C -= V D' and the new trailing norms (pass 2).  The Z
+    // columns are numbered in column order (b last) and split evenly over
+    // the team, in batches of CB columns per CTA.  V's triangular structure
+    // (zero above row t, v0 on row t) is folded into the staged rows.  Every
+    // sum runs in an order fixed by kp alone.
+    if (kp <= 0) {
+      nP += kp;
+      return sync();
+    }
+    const int VS = kp | 1;                          // odd row stride of staged V rows
+    double* s_D = dyn;                              // KM x CB
+    double* s_E = dyn + KM * CB;                    // KM x CB
+    double* wk = dyn + 2 * KM * CB;                 // work area
+    constexpr int WKD = DYN_SMEM / 8 - 2 * KM * CB; // its size in doubles
+    const int RC1 = min(1024, (WKD / (VS + CB)) & ~31);  // pass-1 rows per chunk
+    const int RC2 = (WKD / VS >= 512) ? 512 : (WKD / VS >= 256) ? 256 : (WKD / VS >= 128) ? 128 : 64;
     __shared__ double s_T[KM * KM / 2 + KM];
     __shared__ double s_vt[KM];
-    __shared__ double s_nrm[NW][2];
+    __shared__ double s_nrm[NW * CB];
     __shared__ int s_cid[CB];
+    __shared__ int s_list[CAND_LOCAL_MAX + 1];
+    __shared__ int s_nl;
     for (int e = tid; e < kp * kp; e += NT) {
       const int t = e / kp, sidx = e - t * kp;
       if (sidx <= t) s_T[t * (t + 1) / 2 + sidx] = ldcg(I.T + sidx + t * KM);
     }
     if (tid < kp) s_vt[tid] = ldcg(I.vtop + tid);
-    int c0, c1;
-    split(I.n, tm.size, tm.rank, c0, c1);
-    const bool do_b = (tm.rank == tm.size - 1);
-    __shared__ int s_list[CAND_LOCAL_MAX + 1];
-    __shared__ int s_nl;
-    if (tid == 0) s_nl = 0;
-    __syncthreads();
-    for (int c = c0 + tid; c < c1; c += NT) {
-      bool z = ldcg(I.pos + c) < 0;
-      for (int t = 0; t < kp && z; ++t) z = (s_J[t] != c);
-      if (z) s_list[atomicAdd(&s_nl, 1)] = c;
+    {
+      // bitmaps of J and of Z; warp 0 ranks the Z columns and keeps this
+      // CTA's share (ascending, b = -1 last)
+      const int nwd = (I.n + 31) >> 5;
+      unsigned* s_jb = reinterpret_cast<unsigned*>(wk);
+      unsigned* s_zb = s_jb + nwd;
+      for (int i = tid; i < nwd; i += NT) s_jb[i] = 0u;
+      __syncthreads();
+      if (tid < kp) atomicOr(&s_jb[s_J[tid] >> 5], 1u << (s_J[tid] & 31));
+      __syncthreads();
+      for (int wd = warp; wd < nwd; wd += NW) {
+        const int c = wd * 32 + lane;
+        const bool z = c < I.n && ldcg(I.pos + c) < 0 && !((s_jb[wd] >> lane) & 1u);
+        const unsigned bits = __ballot_sync(0xffffffffu, z);
+        if (lane == 0) s_zb[wd] = bits;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        int nz = 0;
+        for (int w0 = 0; w0 < nwd; w0 += 32) {
+          int cnt = (w0 + lane < nwd) ? __popc(s_zb[w0 + lane]) : 0;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+          nz += cnt;
+        }
+        int lo, hi;
+        split(nz + 1, tm.size, tm.rank, lo, hi);
+        int run = 0;
+        for (int w0 = 0; w0 < nwd && run < hi; w0 += 32) {
+          const unsigned bits = (w0 + lane < nwd) ? s_zb[w0 + lane] : 0u;
+          const int cnt = __popc(bits);
+          int inc = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          int r = run + inc - cnt;  // rank of this word's first Z column
+          if (r < hi && r + cnt > lo) {
+            unsigned bb = bits;
+            while (bb) {
+              const int bit = __ffs(bb) - 1;
+              bb &= bb - 1;
+              if (r >= lo && r < hi) s_list[r - lo] = (w0 + lane) * 32 + bit;
+              ++r;
+            }
+          }
+          run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) {
+          if (nz >= lo && nz < hi) s_list[nz - lo] = -1;
+          s_nl = hi - lo;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const int nl = s_nl + (do_b ? 1 : 0);
-    auto colptr = [&](int k) -> double* {
-      const int id = s_cid[k];
-      return (id >= 0 ? Wcol(id) : I.bt) + nP;
-    };
-    auto stage = [&](int rb, int nr, int nb) {
-      for (int e = tid; e < nr * kp; e += NT) {
-        const int rr = e / kp, t = e - rr * kp, rg = rb + rr;
-        s_V[rr * VS + t] = (rg > t) ? ldcg(I.V + (size_t)rg * KM + t) : (rg == t ? s_vt[t] : 0.0);
-      }
-      for (int e = tid; e < nb * nr; e += NT) {
-        const int cc = e / nr, rr = e - cc * nr;
-        s_X[cc * RC + rr] = ldcg(colptr(cc) + rb + rr);
-      }
-    };
+    const int nl = s_nl;
+    const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
       __syncthreads();
-      if (tid < nb) s_cid[tid] = (base + tid < s_nl) ? s_list[base + tid] : -1;
+      if (tid < nb) s_cid[tid] = s_list[base + tid];
       __syncthreads();
-      const int outputs = kp * nb;
-      // threads per output from kp and the full batch width only, so a
-      // column's sums do not depend on how many columns share its batch
-      int G = 32;
-      while (G > 1 && G * kp * CB > NT) G >>= 1;
-      const int per = NT / G;  // outputs handled per sweep
-      // pass 1: D[t][c] = sum_r v_t[r] x_c[r]; G threads per output split the rows
-      double acc0 = 0.0, acc1 = 0.0;
-      const int o0 = tid / G, o1 = o0 + per, sub = tid - o0 * G;
-      const int t_0 = o0 % max(kp, 1), c_0 = o0 / max(kp, 1);
-      const int t_1 = o1 % max(kp, 1), c_1 = o1 / max(kp, 1);
-      for (int rb = 0; rb < L; rb += RC) {
-        const int nr = min(RC, L - rb);
-        __syncthreads();
-        stage(rb, nr, nb);
-        __syncthreads();
-        if (o0 < outputs)
-          for (int rr = sub; rr < nr; rr += G) acc0 = fma(s_V[rr * VS + t_0], s_X[c_0 * RC + rr], acc0);
-        if (o1 < outputs)
-          for (int rr = sub; rr < nr; rr += G) acc1 = fma(s_V[rr * VS + t_1], s_X[c_1 * RC + rr], acc1);
-      }
-      for (int off = G >> 1; off >= 1; off >>= 1) {
-        acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
-        acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
-      }
-      if (sub == 0) {
-        if (o0 < outputs) s_D[t_0 * CB + c_0] = acc0;
-        if (o1 < outputs) s_D[t_1 * CB + c_1] = acc1;
-      }
-      __syncthreads();
-      // D' = T^T D
-      for (int o = tid; o < outputs; o += NT) {
-        const int t = o % kp, cc = o / kp;
-        double e2 = 0.0;
-        for (int sidx = 0; sidx <= t; ++sidx) e2 = fma(s_T[t * (t + 1) / 2 + sidx], s_D[sidx * CB + cc], e2);
-        s_E[t * CB + cc] = e2;
-      }
-      // pass 2: x -= V d' per (row, column); thread slots k = 0, 1 keep a
-      // fixed column (tid / RC and tid / RC + NT / RC)
-      double nrm0 = 0.0, nrm1 = 0.0;
-      for (int rb = 0; rb < L; rb += RC) {
-        const int nr = min(RC, L - rb);
-        __syncthreads();
-        stage(rb, nr, nb);
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int idx = tid + k * NT;
-          const int cc = idx / RC, rr = idx - cc * RC;
-          if (cc < nb && rr < nr) {
-            double x = s_X[cc * RC + rr];
-            for (int t = 0; t < kp; ++t) x = fma(-s_V[rr * VS + t], s_E[t * CB + cc], x);
-            colptr(cc)[rb + rr] = x;
-            if (rb + rr >= kp) {
-              if (k == 0) nrm0 = fma(x, x, nrm0);
-              else nrm1 = fma(x, x, nrm1);
-            }
-          }
-        }
-      }
-      // norms: each column's slot is held by RC consecutive threads (2 warps)
-      nrm0 = warp_sum(nrm0);
-      nrm1 = warp_sum(nrm1);
-      if (lane == 0) {
-        s_nrm[warp][0] = nrm0;
-        s_nrm[warp][1] = nrm1;
-      }
-      __syncthreads();
-      if (tid < nb) {
-        const int k = tid / (NT / RC), cl = tid - k * (NT / RC);  // column tid in slot k
-        const int w0 = cl * (RC / 32);
-        double v = 0.0;
-        for (int w2 = 0; w2 < RC / 32; ++w2) v += s_nrm[w0 + w2][k];
-        if (s_cid[tid] >= 0) I.u[s_cid[tid]] = sqrt(v);
+      switch (nb) {
+        case 1: commit_batch<1>(cs); break;
+        case 2: commit_batch<2>(cs); break;
+        case 3: commit_batch<3>(cs); break;
+        case 4: commit_batch<4>(cs); break;
+        case 5: commit_batch<5>(cs); break;
+        case 6: commit_batch<6>(cs); break;
+        case 7: commit_batch<7>(cs); break;
+        case 8: commit_batch<8>(cs); break;
+        case 9: commit_batch<9>(cs); break;
+        case 10: commit_batch<10>(cs); break;
+        case 11: commit_batch<11>(cs); break;
+        case 12: commit_batch<12>(cs); break;
+        case 13: commit_batch<13>(cs); break;
+        case 14: commit_batch<14>(cs); break;
+        case 15: commit_batch<15>(cs); break;
+        default: commit_batch<16>(cs); break;
       }
     }
     nP += kp;
