@@ -1432,18 +1432,30 @@ struct Engine {
         I.rslot[np - 1] = sq;
         I.order[np - 1] = -1;
         I.xP[np - 1] = 0.0;
-        I.ctl[C_READY] = 0;
       }
+    }
+    // the rotation log starts empty: every slot holds NaN until its value is
+    // published (each slot is written once, so a reader needs no fence)
+    for (int i = tm.rank * NT + tid; i < nrot; i += tm.size * NT) {
+      I.rotc[i] = __longlong_as_double(0x7ff8000000000000LL);
+      I.rots[i] = __longlong_as_double(0x7ff8000000000000LL);
     }
     if (!sync()) return false;
     phase(PH_CHAIN);
     // (i) rotation chain on R.  Block b covers generating positions
-    // [q + b*DB, q + (b+1)*DB); lane l of warp 0 owns position bs + l.
+    // [q + b*DB, q + (b+1)*DB) on CTA b mod size; lane l of warp 0 owns
+    // position bs + l and carries only what the next rotation needs.  Warp 1
+    // publishes the block's rotations to the log as they appear, then
+    // replays them to write the rotated rows of R.
     const int nblk = (nrot + DB - 1) / DB;
     double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
+    __shared__ double s_ra[DB], s_ri[DB], s_c0[DB];
+    __shared__ int s_prog;  // rotations of the block generated so far (-1: abandoned)
+    volatile int* prog = &s_prog;
     for (int blk = tm.rank; blk < nblk; blk += tm.size) {
       const int bs = q + blk * DB;
       const int bend = min(bs + DB, np - 1);
+      const int nown = bend - bs;
       __syncthreads();
       // rows below bs are the only ones earlier rotations touch: stage the
       // block's own rows (bs+1 .. bs+DB) once
@@ -1453,83 +1465,139 @@ struct Engine {
         if (bs + l < np - 1 && e <= l) v = ldcg(Rcol(ldcg(I.rslot + bs + l)) + bs + 1 + e);
         sB[e * (DB + 1) + l] = v;
       }
+      if (tid == 0) *prog = 0;
       __syncthreads();
-      if (warp != 0) continue;
-      const int pl = bs + lane;
-      const bool act = pl < np - 1;
-      double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
-      double carry = act ? ldcg(col + q) : 0.0;
-      // earlier blocks' rotations, as they are published, 16 at a time with
-      // the column values loaded ahead of the (sequential) carry chain
-      int t = q;
-      bool expired = false;
-      while (t < bs) {
-        int avail = 0;
-        if (lane == 0) {
-          // an expired wait raises the team error flag; the next barrier
-          // then fails in every CTA
-          const bool ok = wait_ge(I.ctl + C_READY, t - q + 1, tm_err());
-          avail = ok ? *(volatile int*)(I.ctl + C_READY) : -1;
-        }
-        avail = __shfl_sync(0xffffffffu, avail, 0);
-        if (avail < 0) { expired = true; break; }
-        const int tend = min(bs, q + avail);
-        while (t < tend) {
-          const int cnt = min(16, tend - t);
-          const double mcs = (lane < cnt) ? ldcg(I.rotc + (t - q) + lane) : 0.0;
-          const double mss = (lane < cnt) ? ldcg(I.rots + (t - q) + lane) : 0.0;
+      if (warp == 0) {
+        const int pl = bs + lane;
+        const bool act = pl < np - 1;
+        double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
+        double carry = act ? ldcg(col + q) : 0.0;
+        // earlier blocks' rotations, as they appear in the log, up to 16 at
+        // a time (lanes 0-15 poll cosines, 16-31 sines); the column values
+        // are loaded before the wait
+        int t = q;
+        bool expired = false;
+        const long long tw0 = gtimer();
+        unsigned spins = 0;
+        while (t < bs) {
+          const int want = min(16, bs - t);
           double bot[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) bot[e] = (act && e < cnt) ? ldcg(col + t + 1 + e) : 0.0;
+          for (int e = 0; e < 16; ++e) bot[e] = (act && e < want) ? ldcg(col + t + 1 + e) : 0.0;
+          const int j = lane & 15;
+          const double* src = (lane < 16 ? I.rotc : I.rots) + (t - q) + j;
+          double rv = 0.0;
+          unsigned okm = 0u;
+          for (;;) {
+            rv = (j < want) ? *(volatile const double*)src : 0.0;
+            const unsigned m = __ballot_sync(0xffffffffu, j < want && !isnan(rv));
+            okm = m & (m >> 16) & 0xffffu;
+            if (okm & 1u) break;
+            if ((++spins & 63u) == 0u) {
+              int bad = 0;
+              if (lane == 0) {
+                int* er = tm_err();
+                bad = (er && *(volatile int*)er) ? 1 : 0;
+                if (!bad && gtimer() - tw0 > WAIT_NS) {
+                  if (er) atomicExch(er, 1);
+                  bad = 1;
+                }
+              }
+              if (__shfl_sync(0xffffffffu, bad, 0)) { expired = true; break; }
+            }
+          }
+          if (expired) break;
+          const int cnt = __ffs(~okm) - 1;  // leading run of published rotations
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            const double cs = __shfl_sync(0xffffffffu, mcs, e), sn = __shfl_sync(0xffffffffu, mss, e);
-            if (e < cnt && act) {
-              col[t + e] = cs * carry + sn * bot[e];
-              carry = -sn * carry + cs * bot[e];
+            if (e < cnt) {
+              const double cs = __shfl_sync(0xffffffffu, rv, e), sn = __shfl_sync(0xffffffffu, rv, 16 + e);
+              if (act) {
+                col[t + e] = cs * carry + sn * bot[e];
+                carry = -sn * carry + cs * bot[e];
+              }
             }
           }
           t += cnt;
         }
-      }
-      if (expired) continue;
-      // own block: one rotation per position from the staged rows; lane e
-      // keeps rotation bs+e and they are published 8 at a time
-      double pcs = 1.0, pss = 0.0;
-      for (t = bs; t < bend; ++t) {
-        const int e = t - bs;
-        double cs = 1.0, sn = 0.0;
-        if (lane == e) {
-          // rotation zeroing bb against a: r = hypot(a, bb), cs = a/r, sn = bb/r,
-          // through one reciprocal square root on the dependent chain
-          const double a = carry, bb = sB[e * (DB + 1) + e];
-          const double r2 = fma(a, a, bb * bb);
-          double rr = 0.0;
-          if (r2 > 0.0) {
-            const double inv = rsqrt(r2);
-            cs = a * inv;
-            sn = bb * inv;
-            rr = r2 * inv;
-          }
-          col[t] = rr;
-          col[t + 1] = 0.0;
+        if (expired) {
+          if (lane == 0) *prog = -1;
+          continue;
         }
-        cs = __shfl_sync(0xffffffffu, cs, e);
-        sn = __shfl_sync(0xffffffffu, sn, e);
-        if (lane == e) { pcs = cs; pss = sn; }
-        if (lane > e && act) {
-          const double bot = sB[e * (DB + 1) + lane];
-          col[t] = cs * carry + sn * bot;
-          carry = -sn * carry + cs * bot;
-        }
-        if ((e & 7) == 7 || t == bend - 1) {
-          if (lane >= (e & ~7) && lane <= e) {
-            I.rotc[bs - q + lane] = pcs;
-            I.rots[bs - q + lane] = pss;
+        s_c0[lane] = carry;
+        // own block: rotation t zeroes R(t+1, position t) = b against
+        // a = R(t, position t).  Every lane forms 1/r = rsqrt(a^2 + b^2) from
+        // the broadcast a, so the dependent chain per position is a shuffle,
+        // an fma, the rsqrt and a multiply; the new row t+1 of lane l is
+        // (a y_l - b x_l)/r.  Only a and 1/r leave the loop.
+        for (t = bs; t < bend; ++t) {
+          const int e = t - bs;
+          const double a = __shfl_sync(0xffffffffu, carry, e);
+          const double b = sB[e * (DB + 1) + e];
+          const double y = sB[e * (DB + 1) + lane];
+          const double num = fma(a, y, -b * carry);
+          const double r2 = fma(a, a, b * b);
+          const bool nz = r2 > 0.0;
+          const double inv = nz ? rsqrt(r2) : 0.0;
+          carry = nz ? inv * num : y;
+          s_ra[e] = a;
+          s_ri[e] = inv;
+          if ((e & 3) == 3 || t == bend - 1) {
+            __threadfence_block();
+            *prog = e + 1;
           }
-          __threadfence();
-          __syncwarp();
-          if (lane == 0) atomicExch(I.ctl + C_READY, t - q + 1);
+        }
+      } else if (warp == 1) {
+        // publish (cosine a/r and sine b/r; r = 0 gives the identity)
+        int done = 0;
+        const long long tw0 = gtimer();
+        unsigned spins = 0;
+        bool gone = false;
+        while (done < nown) {
+          const int pg = __shfl_sync(0xffffffffu, *prog, 0);
+          if (pg < 0) { gone = true; break; }
+          if (pg > done) {
+            __threadfence_block();
+            const int k = done + lane;
+            if (k < pg) {
+              const double a = s_ra[k], inv = s_ri[k], b = sB[k * (DB + 1) + k];
+              I.rots[bs - q + k] = inv != 0.0 ? b * inv : 0.0;
+              I.rotc[bs - q + k] = inv != 0.0 ? a * inv : 1.0;
+            }
+            done = pg;
+          } else if ((++spins & 63u) == 0u) {
+            int bad = 0;
+            if (lane == 0) {
+              int* er = tm_err();
+              bad = (er && *(volatile int*)er) ? 1 : 0;
+              if (!bad && gtimer() - tw0 > WAIT_NS) {
+                if (er) atomicExch(er, 1);
+                bad = 1;
+              }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) { gone = true; break; }
+          }
+        }
+        if (!gone) {
+          // replay with the chain's own arithmetic: rows bs .. bend of the
+          // block's columns (the diagonal r, a zero below it)
+          __threadfence_block();
+          const int pl = bs + lane;
+          if (pl < np - 1) {
+            double* col = Rcol(ldcg(I.rslot + pl));
+            double x = s_c0[lane];
+            for (int e = 0; e < nown && e <= lane; ++e) {
+              const double a = s_ra[e], inv = s_ri[e], b = sB[e * (DB + 1) + e];
+              if (e == lane) {
+                col[bs + e] = fma(a, a, b * b) * inv;
+                col[bs + e + 1] = 0.0;
+              } else {
+                const double y = sB[e * (DB + 1) + lane];
+                col[bs + e] = inv != 0.0 ? inv * fma(a, x, b * y) : x;
+                x = inv != 0.0 ? inv * fma(a, y, -b * x) : y;
+              }
+            }
+          }
         }
       }
     }
