@@ -35,6 +35,7 @@ constexpr int PW = 2112;             // partial-sum slots per CTA (>= KM(KM+1)/2
 // a barrier that follows every read of its previous contents:
 //   [0, KM(KM+1)/2)        candidate Gram pairs (DM)
 //   [0, 2(KM+1))           panel dots, double-buffered by reflector parity
+//   [2(KM+1), 4(KM+1))     panel pivot row, double-buffered by reflector parity
 //   [P_O1, P_O1 + 8)       outer-loop argmax / maxima / sums
 //   P_RS                   residual sum of squares
 constexpr int P_O1 = PW - 16;

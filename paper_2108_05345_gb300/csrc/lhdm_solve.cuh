@@ -564,6 +564,175 @@ struct Engine {
     return sync();
   }
 
+  // Panel with the team's rows held in shared memory (at most PR_MAX rows
+  // per CTA): the same Householder steps as panel(), one barrier per
+  // reflector.  Each CTA keeps rows [q0, q1) of the kk selected columns and
+  // of Q^T b (column kk) for the whole panel; per reflector i it publishes
+  // its dots and, if it owns row i, the pivot row, and after the barrier
+  // every CTA reduces the team's dots itself (fixed order).  The scalars of
+  // a reflector are formed once per CTA and shared; T is built by rank 0
+  // after the last reflector from the saved products z_s = v_s^T v_i.
+  // (FP64 issue is the scarce resource here: every warp instruction counts.)
+  static constexpr int PR_MAX = 64;
+  static constexpr int PS = KM + 1;  // row stride of the staged panel
+  __device__ bool panel_smem(const int* s_J) {
+    const int L = I.m - nP;
+    if (kk > L) kk = L;
+    const int k0 = kk, NL = k0 + 1;
+    int q0, q1;
+    split(L, tm.size, tm.rank, q0, q1);
+    const int nr = q1 - q0;
+    double* sP = dyn;                   // nr x PS: own rows, columns 0..k0 (k0 = Q^T b)
+    double* sZ = dyn + PR_MAX * PS;     // KM x KM, rank 0: z_s of reflector i at sZ[s + i KM]
+    double* sG = sZ + KM * KM;          // reduction scratch (NT doubles)
+    __shared__ double s_sum[KM + 1], s_f[KM + 1], s_piv[KM + 1], s_an[KM], s_bt[KM];
+    __shared__ double s_sc[4];          // alpha, v0, beta, sign
+    __shared__ int s_stop;
+    for (int e = tid; e < nr * NL; e += NT) {
+      const int rr = e / NL, l = e - rr * NL;
+      sP[rr * PS + l] = (l < k0) ? ldcg(Wcol(s_J[l]) + nP + q0 + rr) : ldcg(I.bt + nP + q0 + rr);
+    }
+    if (tid < k0) s_an[tid] = ldcg(I.anorm + s_J[tid]);
+    __syncthreads();
+    // owner of a panel row: the rank whose split range holds it
+    auto owner = [&](int row) {
+      int r = (int)(((long long)row * tm.size) / max(L, 1));
+      int lo, hi;
+      for (;;) {
+        split(L, tm.size, r, lo, hi);
+        if (row < lo) --r;
+        else if (row >= hi) ++r;
+        else return r;
+      }
+    };
+    // thread (gl, gg): column gl, group gg of G
+    const int G = NT / NL, gl = tid % NL, gg = tid / NL;
+    const bool actg = gg < G;
+    int i = 0;
+    for (; i < k0; ++i) {
+      const int pb = (i & 1) * (KM + 1);
+      double* mypart = I.part + (size_t)tm.rank * PW;
+      // dots of column i with every column (and Q^T b) over own rows > i:
+      // rows r0 + gg, r0 + gg + G, ... per thread, then a pairwise tree
+      const int r0 = max(q0, i + 1) - q0;
+      {
+        double sacc = 0.0;
+        if (actg)
+          for (int rr = r0 + gg; rr < nr; rr += G) sacc = fma(sP[rr * PS + gl], sP[rr * PS + i], sacc);
+        if (actg) sG[gg * NL + gl] = sacc;
+        __syncthreads();
+        for (int st = 1; st < G; st <<= 1) {
+          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
+          __syncthreads();
+        }
+        if (tid <= k0) mypart[pb + tid] = sG[tid];
+      }
+      if (i >= q0 && i < q1 && tid <= k0) mypart[2 * (KM + 1) + pb + tid] = sP[(i - q0) * PS + tid];
+      if (!sync()) return false;
+      // every CTA reduces the team's dots: thread (gl, gg) adds ranks gg,
+      // gg + G, ... (loads first), then a pairwise tree over gg; the pivot
+      // row comes from its owner
+      {
+        const int own = owner(i);
+        if (tid <= k0) s_piv[tid] = ldcg(I.part + (size_t)own * PW + 2 * (KM + 1) + pb + tid);
+        if (actg) {
+          const int cnt = (tm.size - gg + G - 1) / G;
+          double a0 = 0.0, a1 = 0.0;
+          for (int j0 = 0; j0 < cnt; j0 += 4) {
+            double v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              v[k] = (j0 + k < cnt) ? ldcg(I.part + (size_t)(gg + (j0 + k) * G) * PW + pb + gl) : 0.0;
+            a0 += v[0];
+            if (j0 + 1 < cnt) a1 += v[1];
+            if (j0 + 2 < cnt) a0 += v[2];
+            if (j0 + 3 < cnt) a1 += v[3];
+          }
+          sG[gg * NL + gl] = a0 + a1;
+        }
+        __syncthreads();
+        for (int st = 1; st < G; st <<= 1) {
+          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
+          __syncthreads();
+        }
+      }
+      // the reflector's scalars, once per CTA (warp 0), and f for every column
+      if (warp == 0) {
+        const double ssum_i = sG[i];
+        if (lane == 0) {
+          const double xii = s_piv[i];
+          const double alpha = sqrt(fma(xii, xii, ssum_i));
+          const int stop = (i >= L || !(alpha > (100.0 * EPS) * s_an[i])) ? 1 : 0;
+          const double sg = (xii >= 0.0) ? 1.0 : -1.0;
+          const double v0 = xii + sg * alpha;
+          s_stop = stop;
+          s_sc[0] = alpha;
+          s_sc[1] = v0;
+          s_sc[2] = stop ? 0.0 : 2.0 / fma(v0, v0, ssum_i);
+          s_sc[3] = sg;
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+      const double v0 = s_sc[1], beta = s_sc[2];
+      if (tid <= k0) {
+        const double ssum = sG[tid];
+        s_sum[tid] = ssum;
+        s_f[tid] = (tid > i) ? beta * fma(v0, s_piv[tid], ssum) : 0.0;
+        if (tm.rank == 0 && tid < i) sZ[tid + i * KM] = fma(s_piv[tid], v0, ssum);  // z_s = v_s^T v_i
+      }
+      __syncthreads();
+      if (tm.rank == 0) {
+        if (tid == i) I.R22[i + i * KM] = -s_sc[3] * s_sc[0];
+        if (tid > i && tid < k0) I.R22[i + tid * KM] = s_piv[tid] - s_f[tid] * v0;
+        if (tid == k0) I.pr[i] = s_piv[k0] - s_f[k0] * v0;
+        if (tid == 0) {
+          I.vtop[i] = v0;
+          I.beta[i] = beta;
+          s_bt[i] = beta;
+        }
+      }
+      flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i) + 1) * (double)(L - i));
+      // update own rows > i of the later columns and of Q^T b
+      const int nl = k0 - i;
+      for (int e = tid; e < (nr - r0) * nl; e += NT) {
+        const int rr = r0 + e / nl, l = i + 1 + (e - (e / nl) * nl);
+        sP[rr * PS + l] = fma(-s_f[l], sP[rr * PS + i], sP[rr * PS + l]);
+      }
+      __syncthreads();
+    }
+    kk = i;  // reflectors formed (truncated by the rank bound)
+    // V rows of this CTA (reflector components below the diagonal)
+    for (int e = tid; e < nr * kk; e += NT) {
+      const int rr = e / kk, t = e - rr * kk;
+      I.V[(size_t)(q0 + rr) * KM + t] = sP[rr * PS + t];
+    }
+    if (tm.rank == 0) {
+      // T column by column: T[c, c] = beta_c, T[0:c, c] = -beta_c T[0:c, 0:c] z_c
+      // (thread r computes row r; sG holds T column-major with stride KM)
+      double* sT = sG + NT;  // KM x KM, column-major
+      for (int c = 0; c < kk; ++c) {
+        if (tid < c) {
+          double c0 = 0.0, c1 = 0.0;
+          int sidx = tid;
+          for (; sidx + 1 < c; sidx += 2) {
+            c0 = fma(sT[tid + sidx * KM], sZ[sidx + c * KM], c0);
+            c1 = fma(sT[tid + (sidx + 1) * KM], sZ[sidx + 1 + c * KM], c1);
+          }
+          if (sidx < c) c0 = fma(sT[tid + sidx * KM], sZ[sidx + c * KM], c0);
+          sT[tid + c * KM] = -s_bt[c] * (c0 + c1);
+        }
+        if (tid == c) sT[c + c * KM] = s_bt[c];
+        __syncthreads();
+      }
+      for (int e = tid; e < kk * kk; e += NT) {
+        const int c = e / kk, r = e - c * kk;
+        if (r <= c) I.T[r + c * KM] = sT[r + c * KM];
+      }
+    }
+    return sync();
+  }
+
   // Back substitution with the kk x kk triangle R22 (one warp).
   __device__ void solve_r22(int k, double* y) {
     double a0 = (lane < k) ? ldcg(I.pr + lane) : 0.0;
@@ -1849,7 +2018,11 @@ struct Engine {
       if (!dm_select(s_J)) return fail_out();
       kdm = kk;
       phase(PH_PANEL);
-      if (!panel(s_J)) return fail_out();
+      {
+        const int Lp = I.m - nP;
+        const bool in_smem = (Lp + tm.size - 1) / tm.size <= PR_MAX && tm.size <= 24 * (NT / (KM + 1));
+        if (!(in_smem ? panel_smem(s_J) : panel(s_J))) return fail_out();
+      }
       if (kk == 0) {
         rank_limited = 1;
         break;
