@@ -1699,13 +1699,16 @@ struct Engine {
         // the broadcast a, so the dependent chain per position is a shuffle,
         // an fma, the rsqrt and a multiply; the new row t+1 of lane l is
         // (a y_l - b x_l)/r.  Only a and 1/r leave the loop.
+        // (the next position's b, b^2 and y are loaded a step ahead)
+        double b = sB[0], y = sB[lane];
+        double bb = b * b;
         for (t = bs; t < bend; ++t) {
           const int e = t - bs;
           const double a = __shfl_sync(0xffffffffu, carry, e);
-          const double b = sB[e * (DB + 1) + e];
-          const double y = sB[e * (DB + 1) + lane];
+          const int en = min(e + 1, DB - 1);
+          const double b_n = sB[en * (DB + 1) + en], y_n = sB[en * (DB + 1) + lane];
           const double num = fma(a, y, -b * carry);
-          const double r2 = fma(a, a, b * b);
+          const double r2 = fma(a, a, bb);
           const bool nz = r2 > 0.0;
           const double inv = nz ? rsqrt(r2) : 0.0;
           carry = nz ? inv * num : y;
@@ -1715,6 +1718,9 @@ struct Engine {
             __threadfence_block();
             *prog = e + 1;
           }
+          b = b_n;
+          y = y_n;
+          bb = b_n * b_n;
         }
       } else if (warp == 1) {
         // publish (cosine a/r and sine b/r; r = 0 gives the identity)
