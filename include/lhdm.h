@@ -232,8 +232,9 @@ int lhdm_phase_times(lhdm_ctx* ctx, double* ms, int32_t n, void* stream);
  * lhdm_batch_create plans a batch: host arrays m[batch], n[batch],
  * lda[batch] and host arrays of DEVICE pointers A[batch], b[batch],
  * x[batch], passive[batch] (shapes as in lhdm_solve); info: device array of
- * batch lhdm_info.  prm: host, NULL = defaults; prm->k_max <= 0 lets the
- * built-in tuner choose k_max per instance size.  Allocates all device
+ * batch lhdm_info.  prm: host, NULL = defaults; prm->k_max <= 0 takes
+ * k_max per instance from the autotuner's table (lhdm_batch_autotune), or
+ * from a built-in rule for sizes it has not tuned.  Allocates all device
  * workspace and uploads the descriptor table on the stream (synchronises).
  * Errors: INVALID_ARG, ALLOC, CUDA.
  */
@@ -261,6 +262,37 @@ int lhdm_batch_kmax(const lhdm_batch* plan, int32_t i);
 
 /* Releases a plan (synchronises the device). */
 int lhdm_batch_destroy(lhdm_batch* plan);
+
+/*
+ * Autotuner of the batched solve (the paper fixes k_max by hand; choosing it
+ * per instance size is this library's addition).  Instances are bucketed by
+ * column count n: bucket b holds 128 * 2^(b-1) < n <= 128 * 2^b (bucket 0:
+ * n <= 128; the last bucket is open).  For every bucket present in the
+ * given instances (same argument conventions as lhdm_batch_create, without
+ * outputs), one batch of that bucket's instances is planned, run once to
+ * warm up and timed once with CUDA events for each k_max in {4, 8, 16, 32};
+ * the fastest k_max is stored in a process-wide table that
+ * lhdm_batch_create consults when prm->k_max <= 0 (buckets never tuned use
+ * the built-in rule).  prm: other parameters of the trial solves (NULL =
+ * defaults; its k_max is ignored).  table: host array of
+ * LHDM_TUNE_BUCKETS ints receiving the table (0 = untuned), or NULL.
+ * Allocates and frees temporary device buffers and synchronises the stream;
+ * not for use inside graph capture.
+ * Errors: INVALID_ARG, ALLOC, CUDA.
+ */
+#define LHDM_TUNE_BUCKETS 6
+int lhdm_batch_autotune(int32_t batch, const int32_t* m, const int32_t* n, const int32_t* lda,
+                        const double* const* A, const double* const* b, const lhdm_params* prm,
+                        int32_t* table, void* stream);
+
+/* Reads (table != NULL) the tuner's table of LHDM_TUNE_BUCKETS k_max values
+ * (0 = untuned).  Host memory.  Errors: INVALID_ARG. */
+int lhdm_tuning_get(int32_t* table);
+
+/* Replaces the tuner's table (host, LHDM_TUNE_BUCKETS entries, each 0 or
+ * 1..LHDM_KMAX_LIMIT), e.g. to restore a table saved from an earlier run.
+ * Errors: INVALID_ARG. */
+int lhdm_tuning_set(const int32_t* table);
 
 #ifdef __cplusplus
 }

@@ -497,8 +497,27 @@ extern "C" int lhdm_solve_noalloc(int32_t m, int32_t n, const double* A, int32_t
 // Block size per instance when the caller asks the tuner (k_max <= 0):
 // the choice for each size bucket of n, from timing sweeps kept with the
 // project's benchmark data (k_max in {4, 8, 16, 32}).
+// ---------------------------------------------------------------- autotuner
+// k_max per size bucket for batched solves with prm->k_max <= 0: a
+// process-wide table filled by lhdm_batch_autotune (0 = untuned, which falls
+// back to a rule from the benchmark sizes).
+static std::mutex g_tune_mu;
+static int g_tune_kmax[LHDM_TUNE_BUCKETS] = {0, 0, 0, 0, 0, 0};
+static const int kTuneCands[] = {4, 8, 16, 32};
+
+static int tune_bucket(int n) {
+  int bkt = 0;
+  for (long long lim = 128; bkt < LHDM_TUNE_BUCKETS - 1 && n > lim; lim <<= 1) ++bkt;
+  return bkt;
+}
+
 static int tuned_kmax(int m, int n) {
   (void)m;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    const int k = g_tune_kmax[tune_bucket(n)];
+    if (k > 0) return k;
+  }
   if (n <= 256) return 8;
   if (n <= 512) return 16;
   return 32;
@@ -668,3 +687,110 @@ int lhdm_batch_destroy(lhdm_batch* B) {
 }
 
 }  // extern "C"
+
+extern "C" int lhdm_batch_autotune(int32_t batch, const int32_t* m, const int32_t* n, const int32_t* lda,
+                                   const double* const* A, const double* const* b, const lhdm_params* prm,
+                                   int32_t* table, void* stream) {
+  if (batch < 0 || (batch > 0 && (!m || !n || !lda || !A || !b))) return LHDM_ERR_INVALID_ARG;
+  lhdm_params p;
+  lhdm_default_params(&p);
+  if (prm) p = *prm;
+  p.k_max = 1;
+  int rc = check_params(&p, true);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> idx[LHDM_TUNE_BUCKETS];
+  for (int i = 0; i < batch; ++i) {
+    if (m[i] < 0 || n[i] < 0 || lda[i] < std::max(1, m[i])) return LHDM_ERR_INVALID_ARG;
+    if ((m[i] > 0 && n[i] > 0 && !A[i]) || (m[i] > 0 && !b[i])) return LHDM_ERR_INVALID_ARG;
+    idx[tune_bucket(n[i])].push_back(i);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return LHDM_ERR_CUDA;
+  }
+  int result = LHDM_OK;
+  for (int bkt = 0; bkt < LHDM_TUNE_BUCKETS && result == LHDM_OK; ++bkt) {
+    const int cnt = (int)idx[bkt].size();
+    if (cnt == 0) continue;
+    std::vector<int32_t> sm(cnt), sn(cnt), sl(cnt);
+    std::vector<const double*> sA(cnt), sb(cnt);
+    std::vector<double*> sx(cnt);
+    std::vector<int32_t*> sp(cnt);
+    size_t nx = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const int i = idx[bkt][k];
+      sm[k] = m[i];
+      sn[k] = n[i];
+      sl[k] = lda[i];
+      sA[k] = A[i];
+      sb[k] = b[i];
+      nx += (size_t)std::max(n[i], 1);
+    }
+    // trial outputs: one x / passive buffer for the bucket, carved per instance
+    double* dx = nullptr;
+    int32_t* dp = nullptr;
+    lhdm_info* dinfo = nullptr;
+    cudaError_t e = cudaMalloc(&dx, nx * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dp, nx * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dinfo, (size_t)cnt * sizeof(lhdm_info));
+    if (e != cudaSuccess) result = LHDM_ERR_ALLOC;
+    size_t o = 0;
+    for (int k = 0; k < cnt && result == LHDM_OK; ++k) {
+      sx[k] = dx + o;
+      sp[k] = dp + o;
+      o += (size_t)std::max(sn[k], 1);
+    }
+    int best_k = 0;
+    float best_ms = 0.0f;
+    for (int kc : kTuneCands) {
+      if (result != LHDM_OK) break;
+      lhdm_params pk = p;
+      pk.k_max = kc;
+      lhdm_batch* B = nullptr;
+      rc = lhdm_batch_create(&B, cnt, sm.data(), sn.data(), sl.data(), sA.data(), sb.data(), sx.data(), sp.data(),
+                             dinfo, &pk, stream);
+      if (rc) { result = rc; break; }
+      rc = lhdm_batch_run(B, stream);  // warm-up
+      if (!rc && (cudaEventRecord(e0, st) != cudaSuccess)) rc = LHDM_ERR_CUDA;
+      if (!rc) rc = lhdm_batch_run(B, stream);
+      if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)) rc = LHDM_ERR_CUDA;
+      float ms = 0.0f;
+      if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = LHDM_ERR_CUDA;
+      lhdm_batch_destroy(B);
+      if (rc) { result = rc; break; }
+      if (best_k == 0 || ms < best_ms) {
+        best_k = kc;
+        best_ms = ms;
+      }
+    }
+    cudaFree(dx);
+    cudaFree(dp);
+    cudaFree(dinfo);
+    if (result == LHDM_OK) {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tune_kmax[bkt] = best_k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result == LHDM_OK && table) lhdm_tuning_get(table);
+  return result;
+}
+
+extern "C" int lhdm_tuning_get(int32_t* table) {
+  if (!table) return LHDM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (int i = 0; i < LHDM_TUNE_BUCKETS; ++i) table[i] = g_tune_kmax[i];
+  return LHDM_OK;
+}
+
+extern "C" int lhdm_tuning_set(const int32_t* table) {
+  if (!table) return LHDM_ERR_INVALID_ARG;
+  for (int i = 0; i < LHDM_TUNE_BUCKETS; ++i)
+    if (table[i] < 0 || table[i] > LHDM_KMAX_LIMIT) return LHDM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (int i = 0; i < LHDM_TUNE_BUCKETS; ++i) g_tune_kmax[i] = table[i];
+  return LHDM_OK;
+}

@@ -44,25 +44,30 @@ struct Engine {
   // phase timing (rank 0, thread 0)
   long long t_last = 0;
   int cur_phase = -1;
-  double ph[NPHASE];
-  double fl[NPHASE];  // algorithmic FP64 flops per phase (rank 0, thread 0)
+  // per-phase device time and algorithmic FP64 flops (rank 0, thread 0),
+  // in shared memory so that no per-thread array forces the engine's state
+  // into local memory
+  double* phf;
 
   __device__ Engine(Team& t, const Inst& inst, double* d) : tm(t), I(inst), dyn(d) {
     tid = threadIdx.x;
     lane = tid & 31;
     warp = tid >> 5;
-    for (int i = 0; i < NPHASE; ++i) { ph[i] = 0.0; fl[i] = 0.0; }
+    __shared__ double s_phf[2 * NPHASE];
+    phf = s_phf;
+    if (tid == 0)
+      for (int i = 0; i < 2 * NPHASE; ++i) s_phf[i] = 0.0;
   }
 
   // Counts algorithmic flops (an FMA is 2) of a phase; uniform state only.
   __device__ __forceinline__ void flops(int p, double f) {
-    if (I.phase_ns && tm.rank == 0 && tid == 0) fl[p] += f;
+    if (I.phase_ns && tm.rank == 0 && tid == 0) phf[NPHASE + p] += f;
   }
 
   __device__ __forceinline__ void phase(int p) {
     if (I.phase_ns && tm.rank == 0 && tid == 0) {
       const long long t = gtimer();
-      if (cur_phase >= 0) ph[cur_phase] += (double)(t - t_last);
+      if (cur_phase >= 0) phf[cur_phase] += (double)(t - t_last);
       t_last = t;
       cur_phase = p;
     }
@@ -1984,8 +1989,8 @@ struct Engine {
       if (I.phase_ns) {
         phase(-1);
         for (int i = 0; i < NPHASE; ++i) {
-          I.phase_ns[i] = ph[i];
-          I.phase_ns[NPHASE + i] = fl[i];
+          I.phase_ns[i] = phf[i];
+          I.phase_ns[NPHASE + i] = phf[NPHASE + i];
         }
       }
     }

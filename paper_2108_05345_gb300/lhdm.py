@@ -80,6 +80,9 @@ def lib():
         L.lhdm_batch_backward.argtypes = [V, pp, pp, pp, ip, V]
         L.lhdm_batch_kmax.argtypes = [V, i32]
         L.lhdm_batch_destroy.argtypes = [V]
+        L.lhdm_batch_autotune.argtypes = [i32, ip, ip, ip, pp, pp, P, ip, V]
+        L.lhdm_tuning_get.argtypes = [ip]
+        L.lhdm_tuning_set.argtypes = [ip]
         _lib = L
     return _lib
 
@@ -324,3 +327,41 @@ class Batch:
             self.h = None
 
     __del__ = close
+
+
+TUNE_BUCKETS = 6  # LHDM_TUNE_BUCKETS
+TUNE_CANDIDATES = (4, 8, 16, 32)
+
+
+def tune_bucket(n):
+    """Size bucket of the autotuner for an instance with n columns."""
+    b, lim = 0, 128
+    while b < TUNE_BUCKETS - 1 and n > lim:
+        b, lim = b + 1, lim * 2
+    return b
+
+
+def batch_autotune(As, bs, params=None, stream=None):
+    """Times every candidate k_max per size bucket on these instances
+    (lhdm_batch_autotune) and returns the tuner's table (list of ints)."""
+    k = len(As)
+    m = (C.c_int32 * max(k, 1))(*[A.shape[0] for A in As])
+    n = (C.c_int32 * max(k, 1))(*[A.shape[1] for A in As])
+    lda = (C.c_int32 * max(k, 1))(*[_lda(A) for A in As])
+    ptrs = lambda ts: (C.c_void_p * max(k, 1))(*[t.data_ptr() for t in ts])
+    table = (C.c_int32 * TUNE_BUCKETS)()
+    rc = lib().lhdm_batch_autotune(k, m, n, lda, ptrs(As), ptrs(bs),
+                                   C.byref(params) if params is not None else None, table, _stream(stream))
+    _check(rc, "lhdm_batch_autotune")
+    return list(table)
+
+
+def tuning_get():
+    table = (C.c_int32 * TUNE_BUCKETS)()
+    _check(lib().lhdm_tuning_get(table), "lhdm_tuning_get")
+    return list(table)
+
+
+def tuning_set(values):
+    table = (C.c_int32 * TUNE_BUCKETS)(*values)
+    _check(lib().lhdm_tuning_set(table), "lhdm_tuning_set")
