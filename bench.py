@@ -145,6 +145,182 @@ def once(args):
     return 0
 
 
+
+def kernel_sources_sha256():
+    """Hash of the sources the solve kernel is built from (CUDA sources and
+    the C header): a stored ncu traffic figure only applies to this hash."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_05345_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "lhdm.h"), "rb").read())
+    return h.hexdigest()
+
+
+def stored_traffic(workload_tag):
+    """DRAM bytes per launch of the solve kernel from the committed ncu
+    summary of this workload, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "lhdm_solve_grid_kernel_%s_ncu.md" % workload_tag)
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- `"):
+                k, v = line[3:].split("`", 1)
+                kv[k] = v.split(":", 1)[1].strip()
+        if kv.get("sources_sha256") == kernel_sources_sha256():
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def batched_section(lhdm, WL, torch, np):
+    """Batched uneven workload (1024 instances, m ~ U{64..512}, n = 2m): k_max
+    per size bucket from the autotuner, one persistent launch replayed from a
+    captured CUDA graph, against a loop of single solves (a sample)."""
+    inst = WL.batched_uneven(batch_seed=0, count=1024)
+    As = [lhdm.colmajor(torch.from_numpy(A).cuda()) for A, _, _ in inst]
+    bs = [torch.from_numpy(b).cuda() for _, b, _ in inst]
+    table = lhdm.batch_autotune(As, bs, lhdm.default_params())
+    batch = lhdm.Batch(As, bs, lhdm.default_params(k_max=0))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.run(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.run(stream)
+    g.replay()
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / reps
+    infos = batch.info()
+    ok = all(i["status"] == 0 for i in infos)
+    # loop of single solves (one whole-GPU launch each) on a sample, same k_max
+    sample = list(range(0, 1024, 8))
+    ctx = lhdm.Context(max(A.shape[0] for A in As), max(A.shape[1] for A in As))
+    worst, same_p = 0.0, True
+    ts = []
+    for i in sample:
+        prm = lhdm.default_params(k_max=batch.kmax(i))
+        ctx.solve(As[i], bs[i], prm)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, p, _ = ctx.solve(As[i], bs[i], prm, sync=False)
+        c.record()
+        ts.append((a, c))
+        xb = batch.xs[i]
+        worst = max(worst, float(torch.linalg.norm(xb - x) / max(float(torch.linalg.norm(x)), 1e-300)))
+        same_p = same_p and bool(torch.equal(batch.ps[i], p))
+    torch.cuda.synchronize()
+    ms_single = float(np.mean([a.elapsed_time(c) for a, c in ts]))
+    ctx.close()
+    batch.close()
+    return {
+        "workload": "1024 instances, m ~ U{64..512}, n = 2m, A ~ N(0,1/m), 10% nonzeros U(0.1,1], "
+                    "b = A x0 + N(0,1e-3), batch seed 0",
+        "kmax_table": table, "ms_per_batch": ms_batch, "solves_per_s": 1024 * 1000.0 / ms_batch,
+        "graph": True, "all_status_ok": ok,
+        "loop_of_single_solves": {"ms_per_solve": ms_single, "solves_per_s": 1000.0 / ms_single,
+                                  "sample": "every 8th instance (128), same k_max, one launch each"},
+        "speedup_vs_loop": (1024.0 / ms_batch) / (1.0 / ms_single),
+        "parity_vs_single": {"max_rel_err": worst, "passive_identical": same_p},
+    }
+
+
+def layer_section(lhdm, WL, torch, np):
+    """NNLS layer workload (256 instances of A 512x1024): batched forward
+    (k_max = 32) and the batched adjoint for L = ||x - x_target||^2, against
+    per-instance solve + backward on a sample."""
+    inst = WL.layer_batch(count=256)
+    As = [lhdm.colmajor(torch.from_numpy(A).cuda()) for A, _, _, _ in inst]
+    bs = [torch.from_numpy(b).cuda() for _, b, _, _ in inst]
+    xt = [torch.from_numpy(t).cuda() for _, _, _, t in inst]
+    prm = lhdm.default_params(k_max=32)
+    batch = lhdm.Batch(As, bs, prm)
+    batch.run()
+    torch.cuda.synchronize()
+    gs = [2.0 * (x - t) for x, t in zip(batch.xs, xt)]
+    batch.backward(gs)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    batch.run()
+    e[1].record()
+    torch.cuda.synchronize()
+    gs = [2.0 * (x - t) for x, t in zip(batch.xs, xt)]
+    torch.cuda.synchronize()
+    e[1].record()
+    dbs, dAs = batch.backward(gs)
+    e[2].record()
+    torch.cuda.synchronize()
+    ms_f, ms_b = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    ok = all(i["status"] == 0 for i in batch.info())
+    ctx = lhdm.Context(512, 1024)
+    worst_x, worst_db, worst_dA = 0.0, 0.0, 0.0
+    tf, tb = [], []
+    for i in range(0, 256, 8):
+        a, c, d = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        x, p, _ = ctx.solve(As[i], bs[i], prm, sync=False)
+        c.record()
+        db, dA = ctx.backward(As[i], 2.0 * (x - xt[i]))
+        d.record()
+        torch.cuda.synchronize()
+        tf.append(a.elapsed_time(c))
+        tb.append(c.elapsed_time(d))
+        rel = lambda u, v: float(torch.linalg.norm(u - v) / max(float(torch.linalg.norm(v)), 1e-300))
+        worst_x = max(worst_x, rel(batch.xs[i], x))
+        worst_db = max(worst_db, rel(dbs[i], db))
+        worst_dA = max(worst_dA, rel(dAs[i], dA))
+    ctx.close()
+    batch.close()
+    return {
+        "workload": "256 instances of A 512x1024 ~ N(0,1/512), 40 nonzeros U(0.1,1], b = A x0 + N(0,1e-3), "
+                    "L = ||x - x_target||^2, x_target = x0 + 1e-2 xi",
+        "k_max": 32, "forward_ms": ms_f, "backward_ms": ms_b,
+        "solves_per_s": 256 * 1000.0 / ms_f, "all_status_ok": ok,
+        "single": {"forward_ms_per_instance": float(np.mean(tf)), "backward_ms_per_instance": float(np.mean(tb)),
+                   "sample": "every 8th instance (32)"},
+        "parity_vs_single": {"x": worst_x, "dLdb": worst_db, "dLdA": worst_dA},
+    }
+
+
+def sparse_section(lhdm, WL, torch, np, s=256):
+    """Sparse-recovery instance (A 2048x8192 Gaussian, unit-norm columns,
+    s nonzeros, noiseless): LHDM k_max = 64 vs one-column LH."""
+    A, b, x0 = WL.sparse_recovery_sweep(0, s)
+    At = lhdm.colmajor(torch.from_numpy(A).cuda())
+    bt = torch.from_numpy(b).cuda()
+    ctx = lhdm.Context(*A.shape)
+    out = {"workload": "A 2048x8192 N(0,1) unit-norm columns, x0 %d nonzeros U(0.1,1], b = A x0, seed 0" % s}
+    for name, k in (("lhdm_k64", 64), ("lh", 1)):
+        prm = lhdm.default_params(k_max=k)
+        ctx.solve(At, bt, prm)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, p, _ = ctx.solve(At, bt, prm, sync=False)
+        c.record()
+        torch.cuda.synchronize()
+        info = ctx.info()
+        xr = x.cpu().numpy()
+        out[name] = {"ms": a.elapsed_time(c), "n_outer": int(info["n_outer"]),
+                     "recovery_rel_err": float(np.linalg.norm(xr - x0) / np.linalg.norm(x0)),
+                     "support_exact": sorted(np.flatnonzero(xr > 0).tolist()) == sorted(np.flatnonzero(x0 > 0).tolist())}
+    out["speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k64"]["ms"]
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +330,8 @@ def main():
     ap.add_argument("--kmax", type=int, default=32)
     ap.add_argument("--lh-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and parity leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, layer and sparse-recovery workloads reported beside the headline")
     ap.add_argument("--once", action="store_true",
                     help="profiling mode: exactly one solve of the benchmark instance, no warm-up")
     ap.add_argument("--m", type=int, default=4096, help="rows of the instance (--once only)")
@@ -306,7 +484,8 @@ def main():
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "peak_source": "derived: %.0f DFMA/clk/SM (measured) x %d SMs x %.0f MHz"
                                     % (DFMA_PER_CLK_PER_SM, nsm, sm_mhz_peak),
-                     "algorithmic_flops": flops_total, "traffic": None},
+                     "algorithmic_flops": flops_total, "traffic": stored_traffic("4096x2048"),
+                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/; null if the sources changed since)"},
         "dual_gemv": {"achieved_gbs": dual_gbs, "hbm_peak_gbs": hbm, "hbm_source": hbm_src,
                       "frac_of_hbm": (dual_gbs / hbm) if dual_gbs else None,
                       "fp64_frac": ((fl_ph["dual"] / (ms_ph["dual"] * 1e-3) / 1e12) / fp64_peak) if ms_ph["dual"] else None},
@@ -317,6 +496,10 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_extra and world == 1:
+        line["batched"] = batched_section(lhdm, WL, torch, np)
+        line["layer"] = layer_section(lhdm, WL, torch, np)
+        line["sparse_recovery"] = sparse_section(lhdm, WL, torch, np)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
