@@ -42,6 +42,7 @@ constexpr int P_O1 = PW - 16;
 constexpr int P_RS = PW - 1;
 constexpr int TB = 64;               // triangular-solve block
 constexpr int SLAB = 16;             // rows per accumulation slab of the pipelined solve
+constexpr int INV_PARTS = TB / NW;   // column classes of a diagonal-block inverse (one column per warp)
 constexpr int DB = 32;               // downdate block (positions per warp)
 constexpr int NPHASE = 12;
 constexpr double EPS = 2.220446049250313e-16;  // 2^-52
@@ -102,7 +103,7 @@ struct Inst {
   int* qlist;     // cap: positions removed by the current inner step
   double* Dinv;   // ceil(cap/TB) x TB x TB inverses of R's diagonal blocks (null: no pipelined solve)
   double* accb;   // ceil(cap/TB) x TB slab accumulations of the pipelined solve
-  int* tflag;     // ceil(cap/TB) block flags, then ceil(cap/TB) * TB/SLAB slab flags
+  int* tflag;     // ceil(cap/TB) block flags, ceil(cap/TB) * TB/SLAB slab flags, ceil(cap/TB) * INV_PARTS inverse flags
   unsigned long long* amask;  // KM acceptance masks
   double* phase_ns;           // NPHASE (may be null)
   int* trace;                 // 6 ints per outer step (may be null)

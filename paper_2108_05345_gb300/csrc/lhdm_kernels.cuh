@@ -90,7 +90,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.ipart = take((size_t)team * 8);
   L.ctl = take(16);
   L.qlist = take(cap);
-  L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB) : 1);
+  L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB + INV_PARTS) : 1);
   L.itotal = o;
   return L;
 }

@@ -90,7 +90,7 @@ struct Engine {
   // must follow before the first solve).
   __device__ void clear_tri_flags() {
     if (!I.tflag) return;
-    const int nbk = (I.cap + TB - 1) / TB, nfl = nbk * (1 + TB / SLAB);
+    const int nbk = (I.cap + TB - 1) / TB, nfl = nbk * (1 + TB / SLAB + INV_PARTS);
     for (int i = tm.rank * NT + tid; i < nfl; i += tm.size * NT) I.tflag[i] = 0;
   }
 
@@ -920,8 +920,10 @@ struct Engine {
     if (tm.rank == 0) {
       ok = tri_chain(np, nb, ep);
     } else {
+      // inverse columns first (they wait for nothing; rank 0 may wait for
+      // them), then the slab accumulations
+      tri_inverse(np, nb, ep);
       ok = tri_slabs(np, nb, ep);
-      if (ok) tri_inverse(np, nb);
     }
     if (!ok) {
       failed = true;
@@ -935,6 +937,7 @@ struct Engine {
 
   __device__ __forceinline__ int* yflags() const { return I.tflag; }
   __device__ __forceinline__ int* sflags() const { return I.tflag + (I.cap + TB - 1) / TB; }
+  __device__ __forceinline__ int* iflags() const { return I.tflag + (1 + TB / SLAB) * ((I.cap + TB - 1) / TB); }
 
   // Rank 0: the chain over the blocks (see trsv_pipelined).
   __device__ bool tri_chain(int np, int nb, int ep) {
@@ -947,15 +950,25 @@ struct Engine {
     const int row = tid & (TB - 1), g = tid >> 6;  // 8 groups of 8 columns
     int* yfl = yflags();
     const int* sfl = sflags();
+    const int* ifl = iflags();
     for (int bi = nb - 1; bi >= 0; --bi) {
       const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
       const int c0 = b0 + TB, nc = (bi + 1 < nb) ? min(np, c0 + TB) - c0 : 0;
-      const int v = min(max(inv_valid - b0, 0), nbk);  // columns with a valid inverse
+      int v = min(max(inv_valid - b0, 0), nbk);  // columns with a valid inverse
       double* ycur = s_y[bi & 1];
       const double* ynext = s_y[(bi + 1) & 1];
       if (tid < nbk) s_bslot[tid] = ldcg(I.rslot + b0 + tid);
       if (tid >= TB && tid - TB < nc) s_cslot[tid - TB] = ldcg(I.rslot + c0 + tid - TB);
-      __syncthreads();
+      if (bi < nb - 1 && v < nbk) {
+        // the stale columns of this block are being inverted by the last
+        // ranks in this call: wait for them instead of substituting
+        int okw = 1;
+        if (tid < INV_PARTS) okw = wait_ge(ifl + bi * INV_PARTS + tid, ep, tm_err()) ? 1 : 0;
+        if (!__syncthreads_and(okw)) return false;
+        v = nbk;
+      } else {
+        __syncthreads();
+      }
       // loads that do not wait for y: tile R(b, b+1), inverse columns, rhs,
       // stale columns of the diagonal block
       double rt[8], di[8];
@@ -1113,16 +1126,21 @@ struct Engine {
   // size-1 - k mod (size-1); one warp per column, which solves D x = e_j by
   // column-oriented substitution and writes column j of D^{-1} (zeros below
   // the diagonal).
-  __device__ void tri_inverse(int np, int nb) {
-    constexpr int PARTS = TB / NW;        // 4 column classes, one column per warp
+  __device__ void tri_inverse(int np, int nb, int ep) {
+    constexpr int PARTS = INV_PARTS;      // 4 column classes, one column per warp
     const int bs = inv_valid / TB;
-    const int nitem = PARTS * (nb - bs);
+    const int nstale = nb - bs;
+    const int nitem = PARTS * nstale;
     const int nh = tm.size - 1, h = tm.size - 1 - tm.rank;
     if (nitem <= 0 || h >= nitem) return;
     double* sD = dyn;
     __shared__ double s_ri[TB];
+    int* ifl = iflags();
     for (int it = h; it < nitem; it += nh) {
-      const int bi = bs + it / PARTS, part = it % PARTS;
+      // blocks in the order rank 0 needs them: nb-2, nb-3, ..., bs, and the
+      // last block (which rank 0 substitutes) at the end
+      const int q = it / PARTS, part = it % PARTS;
+      const int bi = (q < nstale - 1) ? nb - 2 - q : nb - 1;
       const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
       const int v = min(max(inv_valid - b0, 0), nbk);
       __syncthreads();  // the previous item's readers of sD are done
@@ -1159,7 +1177,10 @@ struct Engine {
         double* out = I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB;
         out[lane] = (lane <= j) ? a0 : 0.0;
         out[lane + 32] = (lane + 32 <= j) ? a1 : 0.0;
+        __threadfence();
       }
+      __syncthreads();
+      if (tid == 0) atomicExch(ifl + bi * PARTS + part, ep);
     }
   }
 
