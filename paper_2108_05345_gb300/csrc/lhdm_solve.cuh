@@ -157,16 +157,24 @@ struct Engine {
   // CTA's column range: argmax of w over the eligible part of Z (lowest
   // index on ties), max u over it, max w over all of Z, eligible count.
   // Slots 5..7 carry extra sums (amax / ||r||^2 / non-finite count).
-  __device__ void o1_partial(double s5, double s6, double s7) {
+  // The CTA's columns are its range of [0, n), or the given list of Z
+  // columns (the ones it just computed w and u for).
+  __device__ void o1_partial(double s5, double s6, double s7, const int* list = nullptr, int nlist = 0) {
     __shared__ double shv[32];
     __shared__ int shi[32];
     __syncthreads();
     int c0, c1;
-    split(I.n, tm.size, tm.rank, c0, c1);
+    if (list) {
+      c0 = 0;
+      c1 = nlist;
+    } else {
+      split(I.n, tm.size, tm.rank, c0, c1);
+    }
     ArgMax best{0.0, -1};
     double um = -INFINITY, wz = -INFINITY;
     int ne = 0;
-    for (int c = c0 + tid; c < c1; c += NT) {
+    for (int k = c0 + tid; k < c1; k += NT) {
+      const int c = list ? list[k] : k;
       if (ldcg(I.pos + c) >= 0) continue;
       const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
       wz = fmax(wz, wc);
@@ -1185,6 +1193,69 @@ struct Engine {
   }
 
 
+
+  // This CTA's share of the Z columns: the columns with pos < 0 that are not
+  // in J[0:nj] are numbered in column order (with b = -1 appended last when
+  // with_b) and split evenly over the team, so every CTA gets floor or ceil
+  // of the count.  s_list receives the share in ascending order; scratch:
+  // 2 ceil(n/32) words.  Returns the share's size.
+  __device__ int z_share(int* s_list, unsigned* scratch, const int* s_J, int nj, bool with_b) {
+    __shared__ int s_nl;
+    const int nwd = (I.n + 31) >> 5;
+    unsigned* s_jb = scratch;
+    unsigned* s_zb = s_jb + nwd;
+    for (int i = tid; i < nwd; i += NT) s_jb[i] = 0u;
+    __syncthreads();
+    if (tid < nj) atomicOr(&s_jb[s_J[tid] >> 5], 1u << (s_J[tid] & 31));
+    __syncthreads();
+    for (int wd = warp; wd < nwd; wd += NW) {
+      const int c = wd * 32 + lane;
+      const bool z = c < I.n && ldcg(I.pos + c) < 0 && !((s_jb[wd] >> lane) & 1u);
+      const unsigned bits = __ballot_sync(0xffffffffu, z);
+      if (lane == 0) s_zb[wd] = bits;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int nz = 0;
+      for (int w0 = 0; w0 < nwd; w0 += 32) {
+        int cnt = (w0 + lane < nwd) ? __popc(s_zb[w0 + lane]) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        nz += cnt;
+      }
+      int lo, hi;
+      split(nz + (with_b ? 1 : 0), tm.size, tm.rank, lo, hi);
+      int run = 0;
+      for (int w0 = 0; w0 < nwd && run < hi; w0 += 32) {
+        const unsigned bits = (w0 + lane < nwd) ? s_zb[w0 + lane] : 0u;
+        const int cnt = __popc(bits);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        int r = run + inc - cnt;  // rank of this word's first Z column
+        if (r < hi && r + cnt > lo) {
+          unsigned bb = bits;
+          while (bb) {
+            const int bit = __ffs(bb) - 1;
+            bb &= bb - 1;
+            if (r >= lo && r < hi) s_list[r - lo] = (w0 + lane) * 32 + bit;
+            ++r;
+          }
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) {
+        if (with_b && nz >= lo && nz < hi) s_list[nz - lo] = -1;
+        s_nl = hi - lo;
+      }
+    }
+    __syncthreads();
+    return s_nl;
+  }
+
   // Shared-memory layout and chunk sizes of one commit (see commit()).
   struct CommitShape {
     int L, RC1, RC2, VS;
@@ -1407,69 +1478,13 @@ struct Engine {
     __shared__ double s_nrm[NW * CB];
     __shared__ int s_cid[CB];
     __shared__ int s_list[CAND_LOCAL_MAX + 1];
-    __shared__ int s_nl;
     for (int e = tid; e < kp * kp; e += NT) {
       const int t = e / kp, sidx = e - t * kp;
       if (sidx <= t) s_T[t * (t + 1) / 2 + sidx] = ldcg(I.T + sidx + t * KM);
     }
     if (tid < kp) s_vt[tid] = ldcg(I.vtop + tid);
-    {
-      // bitmaps of J and of Z; warp 0 ranks the Z columns and keeps this
-      // CTA's share (ascending, b = -1 last)
-      const int nwd = (I.n + 31) >> 5;
-      unsigned* s_jb = reinterpret_cast<unsigned*>(wk);
-      unsigned* s_zb = s_jb + nwd;
-      for (int i = tid; i < nwd; i += NT) s_jb[i] = 0u;
-      __syncthreads();
-      if (tid < kp) atomicOr(&s_jb[s_J[tid] >> 5], 1u << (s_J[tid] & 31));
-      __syncthreads();
-      for (int wd = warp; wd < nwd; wd += NW) {
-        const int c = wd * 32 + lane;
-        const bool z = c < I.n && ldcg(I.pos + c) < 0 && !((s_jb[wd] >> lane) & 1u);
-        const unsigned bits = __ballot_sync(0xffffffffu, z);
-        if (lane == 0) s_zb[wd] = bits;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        int nz = 0;
-        for (int w0 = 0; w0 < nwd; w0 += 32) {
-          int cnt = (w0 + lane < nwd) ? __popc(s_zb[w0 + lane]) : 0;
-#pragma unroll
-          for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-          nz += cnt;
-        }
-        int lo, hi;
-        split(nz + 1, tm.size, tm.rank, lo, hi);
-        int run = 0;
-        for (int w0 = 0; w0 < nwd && run < hi; w0 += 32) {
-          const unsigned bits = (w0 + lane < nwd) ? s_zb[w0 + lane] : 0u;
-          const int cnt = __popc(bits);
-          int inc = cnt;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-          }
-          int r = run + inc - cnt;  // rank of this word's first Z column
-          if (r < hi && r + cnt > lo) {
-            unsigned bb = bits;
-            while (bb) {
-              const int bit = __ffs(bb) - 1;
-              bb &= bb - 1;
-              if (r >= lo && r < hi) s_list[r - lo] = (w0 + lane) * 32 + bit;
-              ++r;
-            }
-          }
-          run += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (lane == 0) {
-          if (nz >= lo && nz < hi) s_list[nz - lo] = -1;
-          s_nl = hi - lo;
-        }
-      }
-      __syncthreads();
-    }
-    const int nl = s_nl;
+    const int nl_share = z_share(s_list, reinterpret_cast<unsigned*>(wk), s_J, kp, true);
+    const int nl = nl_share;
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
@@ -1879,19 +1894,38 @@ struct Engine {
     __shared__ double s_acc[NW][32];
     double rs = 0.0;
     const int ntile = (I.m + 31) / 32;
+    // the passive order and y_P, staged once if they fit (else read from L2)
+    const bool staged = (size_t)nP * 12 + 16 <= (size_t)DYN_SMEM && tm.rank < ntile;
+    double* s_yv = dyn;
+    int* s_ov = reinterpret_cast<int*>(dyn + nP);
+    if (staged) {
+      for (int p = tid; p < nP; p += NT) {
+        s_yv[p] = ldcg(I.yP + p);
+        s_ov[p] = ldcg(I.order + p);
+      }
+      __syncthreads();
+    }
     for (int tile = tm.rank; tile < ntile; tile += tm.size) {
       const int row = tile * 32 + lane;
       double acc = 0.0, acc2 = 0.0;
       if (row < I.m) {
         int p = warp;
-        for (; p + NW < nP; p += 2 * NW) {
-          const int c = ldcg(I.order + p), c2 = ldcg(I.order + p + NW);
-          acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
-          acc2 = fma(__ldg(I.A + (size_t)c2 * I.lda + row), ldcg(I.yP + p + NW), acc2);
-        }
-        for (; p < nP; p += NW) {
-          const int c = ldcg(I.order + p);
-          acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
+        if (staged) {
+          for (; p + NW < nP; p += 2 * NW) {
+            acc = fma(__ldg(I.A + (size_t)s_ov[p] * I.lda + row), s_yv[p], acc);
+            acc2 = fma(__ldg(I.A + (size_t)s_ov[p + NW] * I.lda + row), s_yv[p + NW], acc2);
+          }
+          for (; p < nP; p += NW) acc = fma(__ldg(I.A + (size_t)s_ov[p] * I.lda + row), s_yv[p], acc);
+        } else {
+          for (; p + NW < nP; p += 2 * NW) {
+            const int c = ldcg(I.order + p), c2 = ldcg(I.order + p + NW);
+            acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
+            acc2 = fma(__ldg(I.A + (size_t)c2 * I.lda + row), ldcg(I.yP + p + NW), acc2);
+          }
+          for (; p < nP; p += NW) {
+            const int c = ldcg(I.order + p);
+            acc = fma(__ldg(I.A + (size_t)c * I.lda + row), ldcg(I.yP + p), acc);
+          }
         }
       }
       s_acc[warp][lane] = acc + acc2;
@@ -1913,56 +1947,94 @@ struct Engine {
     if (tid == 0) I.part[(size_t)tm.rank * PW + P_RS] = rs;
   }
 
-  // w = A^T r on Z (w_P = 0), u refreshed after removals, O1 partial.
+  // w = A^T r on Z (w_P = 0), u refreshed after removals, O1 partial.  The
+  // Z columns are split evenly over the team (z_share) and r is staged in
+  // shared memory; in batches of up to 32 columns, warps take (column,
+  // quarter of the rows) units round-robin and each column's four quarters
+  // are added in a fixed order.
+  static constexpr int DUAL_RMAX = 16384;  // rows of r held in shared memory
   __device__ void dual() {
-    int c0, c1;
-    split(I.n, tm.size, tm.rank, c0, c1);
-    for (int c = c0 + warp; c < c1; c += NW) {
-      if (ldcg(I.pos + c) >= 0) {
-        if (lane == 0) I.w[c] = 0.0;
-        continue;
-      }
-      const double* a = I.A + (size_t)c * I.lda;
-      double sa[8];
+    {
+      int c0, c1;
+      split(I.n, tm.size, tm.rank, c0, c1);
+      for (int c = c0 + tid; c < c1; c += NT)
+        if (ldcg(I.pos + c) >= 0) I.w[c] = 0.0;
+    }
+    const int m = I.m;
+    const bool r_in_smem = m <= DUAL_RMAX &&
+                           (size_t)m * 8 + (CAND_LOCAL_MAX + 2) * 4 + 8 * (size_t)((I.n + 31) / 32) <= (size_t)DYN_SMEM;
+    double* s_r = dyn;                                    // m doubles
+    int* s_zl = reinterpret_cast<int*>(dyn + (r_in_smem ? m : 0));
+    unsigned* scr = reinterpret_cast<unsigned*>(s_zl + CAND_LOCAL_MAX + 2);
+    __shared__ double s_pw[32 * 4], s_pu[32 * 4];
+    __shared__ int s_c[32];
+    const int nl = z_share(s_zl, scr, nullptr, 0, false);
+    if (r_in_smem)
+      for (int i = tid; i < m; i += NT) s_r[i] = ldcg(I.r + i);
+    const double* rv = r_in_smem ? s_r : I.r;
+    const int L = m - nP;
+    for (int base = 0; base < nl; base += 32) {
+      const int nb = min(32, nl - base);
+      __syncthreads();
+      if (tid < nb) s_c[tid] = s_zl[base + tid];
+      __syncthreads();
+      const int nunit = (u_dirty ? 8 : 4) * nb;
+      for (int un = warp; un < nunit; un += NW) {
+        const bool is_u = un >= 4 * nb;
+        const int k = (is_u ? un - 4 * nb : un) >> 2, qq = un & 3;
+        const int c = s_c[k];
+        double sa[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sa[k] = 0.0;
-      int i = lane;
-      for (; i + 224 < I.m; i += 256) {
-        double av[8], rv[8];
+        for (int j = 0; j < 8; ++j) sa[j] = 0.0;
+        if (!is_u) {
+          const double* a = I.A + (size_t)c * I.lda;
+          int i0, i1;
+          split(m, 4, qq, i0, i1);
+          int i = i0 + lane;
+          for (; i + 224 < i1; i += 256) {
+            double av[8], rr[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          av[k] = __ldg(a + i + 32 * k);
-          rv[k] = ldcg(I.r + i + 32 * k);
-        }
+            for (int j = 0; j < 8; ++j) {
+              av[j] = __ldg(a + i + 32 * j);
+              rr[j] = r_in_smem ? rv[i + 32 * j] : ldcg(rv + i + 32 * j);
+            }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sa[k] = fma(av[k], rv[k], sa[k]);
-      }
-      for (; i < I.m; i += 32) sa[0] = fma(__ldg(a + i), ldcg(I.r + i), sa[0]);
-      const double s = warp_sum(((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7])));
-      double un = 0.0;
-      if (u_dirty) {
-        const double* wc = Wcol(c);
-        double u0 = 0.0, u1 = 0.0;
-        int i2 = nP + lane;
-        for (; i2 + 32 < I.m; i2 += 64) {
-          const double v0 = ldcg(wc + i2), v1 = ldcg(wc + i2 + 32);
-          u0 = fma(v0, v0, u0);
-          u1 = fma(v1, v1, u1);
+            for (int j = 0; j < 8; ++j) sa[j] = fma(av[j], rr[j], sa[j]);
+          }
+          for (; i < i1; i += 32) sa[0] = fma(__ldg(a + i), r_in_smem ? rv[i] : ldcg(rv + i), sa[0]);
+        } else {
+          const double* wc = Wcol(c) + nP;
+          int i0, i1;
+          split(L, 4, qq, i0, i1);
+          int i = i0 + lane;
+          for (; i + 224 < i1; i += 256) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = ldcg(wc + i + 32 * j);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sa[j] = fma(v[j], v[j], sa[j]);
+          }
+          for (; i < i1; i += 32) {
+            const double v0 = ldcg(wc + i);
+            sa[0] = fma(v0, v0, sa[0]);
+          }
         }
-        for (; i2 < I.m; i2 += 32) {
-          const double v0 = ldcg(wc + i2);
-          u0 = fma(v0, v0, u0);
-        }
-        un = warp_sum(u0 + u1);
+        const double tot = warp_sum(((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7])));
+        if (lane == 0) (is_u ? s_pu : s_pw)[k * 4 + qq] = tot;
       }
-      if (lane == 0) {
-        I.w[c] = s;
-        if (u_dirty) I.u[c] = sqrt(un);
+      __syncthreads();
+      if (tid < nb) {
+        const double* pw = s_pw + tid * 4;
+        I.w[s_c[tid]] = (pw[0] + pw[1]) + (pw[2] + pw[3]);
+        if (u_dirty) {
+          const double* pu = s_pu + tid * 4;
+          I.u[s_c[tid]] = sqrt((pu[0] + pu[1]) + (pu[2] + pu[3]));
+        }
       }
     }
     // resid sum of squares of this CTA is in part[PW-1]; fold it into slot 6
     const double rs = ldcg(I.part + (size_t)tm.rank * PW + P_RS);
-    o1_partial(0.0, rs, 0.0);
+    o1_partial(0.0, rs, 0.0, s_zl, nl);
   }
 
   // ------------------------------------------------------------ outputs
