@@ -158,84 +158,101 @@ struct Engine {
   // index on ties), max u over it, max w over all of Z, eligible count.
   // Slots 5..7 carry extra sums (amax / ||r||^2 / non-finite count).
   // The CTA's columns are its range of [0, n), or the given list of Z
-  // columns (the ones it just computed w and u for).
+  // columns (the ones it just computed w and u for).  Warp 0 alone scans
+  // them (a handful per CTA) and folds the maxima with shuffles: FP64
+  // reductions on every warp would cost more than the scan.
   __device__ void o1_partial(double s5, double s6, double s7, const int* list = nullptr, int nlist = 0) {
-    __shared__ double shv[32];
-    __shared__ int shi[32];
     __syncthreads();
-    int c0, c1;
-    if (list) {
-      c0 = 0;
-      c1 = nlist;
-    } else {
-      split(I.n, tm.size, tm.rank, c0, c1);
-    }
-    ArgMax best{0.0, -1};
-    double um = -INFINITY, wz = -INFINITY;
-    int ne = 0;
-    for (int k = c0 + tid; k < c1; k += NT) {
-      const int c = list ? list[k] : k;
-      if (ldcg(I.pos + c) >= 0) continue;
-      const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
-      wz = fmax(wz, wc);
-      if (uc > (100.0 * EPS) * an) {
-        ++ne;
-        best = amax_merge(best, ArgMax{wc, c});
-        um = fmax(um, uc);
+    if (warp == 0) {
+      int c0, c1;
+      if (list) {
+        c0 = 0;
+        c1 = nlist;
+      } else {
+        split(I.n, tm.size, tm.rank, c0, c1);
       }
-    }
-    best = block_amax(best, shv, shi);
-    um = block_max(um, shv);
-    wz = block_max(wz, shv);
-    ne = block_sum_int(ne, shi);
-    if (tid == 0) {
-      double* p = I.part + (size_t)tm.rank * PW + P_O1;
-      p[0] = best.v;
-      p[1] = (double)best.i;
-      p[2] = um;
-      p[3] = wz;
-      p[4] = (double)ne;
-      p[5] = s5;
-      p[6] = s6;
-      p[7] = s7;
+      ArgMax best{0.0, -1};
+      double um = -INFINITY, wz = -INFINITY;
+      int ne = 0;
+      for (int k = c0 + lane; k < c1; k += 32) {
+        const int c = list ? list[k] : k;
+        const int pc = ldcg(I.pos + c);
+        const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
+        if (pc >= 0) continue;
+        wz = fmax(wz, wc);
+        if (uc > (100.0 * EPS) * an) {
+          ++ne;
+          best = amax_merge(best, ArgMax{wc, c});
+          um = fmax(um, uc);
+        }
+      }
+      best = warp_amax(best);
+      um = warp_max(um);
+      wz = warp_max(wz);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) ne += __shfl_xor_sync(0xffffffffu, ne, o);
+      if (lane == 0) {
+        double* p = I.part + (size_t)tm.rank * PW + P_O1;
+        p[0] = best.v;
+        p[1] = (double)best.i;
+        p[2] = um;
+        p[3] = wz;
+        p[4] = (double)ne;
+        p[5] = s5;
+        p[6] = s6;
+        p[7] = s7;
+      }
     }
   }
 
-  // Combines the O1 partials of every CTA (same order everywhere).
+  // Combines the O1 partials of every CTA (same order everywhere): warp f
+  // folds field f of the team (all of a lane's loads in flight at once),
+  // warp 0 the argmax pair.
+  __device__ double o1_fold(int f, bool is_max) {
+    double acc = is_max ? -INFINITY : 0.0;
+    for (int t0 = 0; t0 < tm.size; t0 += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int t = t0 + lane + 32 * j;
+        v[j] = (t < tm.size) ? ldcg(I.part + (size_t)t * PW + P_O1 + f) : (is_max ? -INFINITY : 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc = is_max ? fmax(acc, v[j]) : acc + v[j];
+    }
+    return is_max ? warp_max(acc) : warp_sum(acc);
+  }
+
   __device__ void o1_reduce(bool first) {
     __shared__ double s_d[8];
     __shared__ int s_i[2];
     if (warp == 0) {
       ArgMax best{0.0, -1};
-      double um = -INFINITY, wz = -INFINITY, s5 = 0.0, s6 = 0.0, s7 = 0.0;
-      int ne = 0;
-      for (int t = lane; t < tm.size; t += 32) {
-        const double* p = I.part + (size_t)t * PW + P_O1;
-        best = amax_merge(best, ArgMax{ldcg(p + 0), (int)ldcg(p + 1)});
-        um = fmax(um, ldcg(p + 2));
-        wz = fmax(wz, ldcg(p + 3));
-        ne += (int)ldcg(p + 4);
-        if (first) s5 = fmax(s5, ldcg(p + 5)); else s5 += ldcg(p + 5);
-        s6 += ldcg(p + 6);
-        s7 += ldcg(p + 7);
+      for (int t0 = 0; t0 < tm.size; t0 += 32 * 8) {
+        double v[8], ix[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int t = t0 + lane + 32 * j;
+          v[j] = (t < tm.size) ? ldcg(I.part + (size_t)t * PW + P_O1) : 0.0;
+          ix[j] = (t < tm.size) ? ldcg(I.part + (size_t)t * PW + P_O1 + 1) : -1.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) best = amax_merge(best, ArgMax{v[j], (int)ix[j]});
       }
       best = warp_amax(best);
-      um = warp_max(um);
-      wz = warp_max(wz);
-      s5 = first ? warp_max(s5) : warp_sum(s5);
-      s6 = warp_sum(s6);
-      s7 = warp_sum(s7);
-#pragma unroll
-      for (int o = 16; o; o >>= 1) ne += __shfl_xor_sync(0xffffffffu, ne, o);
       if (lane == 0) {
         s_d[0] = best.v;
-        s_d[1] = um;
-        s_d[2] = wz;
-        s_d[3] = s5;
-        s_d[4] = s6;
-        s_d[5] = s7;
         s_i[0] = best.i;
-        s_i[1] = ne;
+      }
+    } else if (warp <= 6) {
+      // warp 1: max u, 2: max w over Z, 3: eligible count, 4: slot 5 (max on
+      // the first call, else sum), 5: slot 6 (sum), 6: slot 7 (sum)
+      const int f = warp + 1;
+      const bool is_max = (f == 2 || f == 3 || (f == 5 && first));
+      const double r = o1_fold(f, is_max);
+      if (lane == 0) {
+        if (f == 4) s_i[1] = (int)r;
+        else s_d[f == 2 ? 1 : f == 3 ? 2 : f - 2] = r;
       }
     }
     __syncthreads();
@@ -1208,11 +1225,23 @@ struct Engine {
     __syncthreads();
     if (tid < nj) atomicOr(&s_jb[s_J[tid] >> 5], 1u << (s_J[tid] & 31));
     __syncthreads();
-    for (int wd = warp; wd < nwd; wd += NW) {
-      const int c = wd * 32 + lane;
-      const bool z = c < I.n && ldcg(I.pos + c) < 0 && !((s_jb[wd] >> lane) & 1u);
-      const unsigned bits = __ballot_sync(0xffffffffu, z);
-      if (lane == 0) s_zb[wd] = bits;
+    for (int w0 = warp; w0 < nwd; w0 += 4 * NW) {
+      int pv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = (w0 + k * NW) * 32 + lane;
+        pv[k] = (w0 + k * NW < nwd && c < I.n) ? ldcg(I.pos + c) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int wd = w0 + k * NW;
+        if (wd < nwd) {
+          const int c = wd * 32 + lane;
+          const bool z = c < I.n && pv[k] < 0 && !((s_jb[wd] >> lane) & 1u);
+          const unsigned bits = __ballot_sync(0xffffffffu, z);
+          if (lane == 0) s_zb[wd] = bits;
+        }
+      }
     }
     __syncthreads();
     if (warp == 0) {
