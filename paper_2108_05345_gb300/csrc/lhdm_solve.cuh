@@ -1460,6 +1460,91 @@ struct Engine {
     }
   }
 
+
+  // Commit for kp <= 4 (one-column LH steps and short J): V staged once for
+  // all L rows, then one warp per column does D = V^T x (lanes over rows,
+  // fixed-order sums), D' = T^T D, x -= V D' and the trailing norm, with no
+  // CTA-wide reduction.  The sums depend on kp alone.
+  template <int KP>
+  __device__ void commit_small(int L, double* sV, const int* s_list, int nl) {
+    for (int e0 = tid; e0 < L * KP; e0 += 8 * NT) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int e = e0 + j * NT, r = e / KP, t = e - r * KP;
+        v[j] = (e < L * KP && r > t) ? ldcg(I.V + (size_t)r * KM + t)
+                                     : ((e < L * KP && r == t) ? ldcg(I.vtop + t) : 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (e0 + j * NT < L * KP) sV[e0 + j * NT] = v[j];
+    }
+    double Tm[KP][KP];
+#pragma unroll
+    for (int a = 0; a < KP; ++a)
+#pragma unroll
+      for (int c = 0; c < KP; ++c) Tm[a][c] = (a <= c) ? ldcg(I.T + a + c * KM) : 0.0;
+    __syncthreads();
+    for (int k = warp; k < nl; k += NW) {
+      const int id = s_list[k];
+      double* x = (id >= 0 ? Wcol(id) : I.bt) + nP;
+      // eight rows per lane in flight in both passes
+      double acc[KP][2];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) acc[t][0] = acc[t][1] = 0.0;
+      int r = lane;
+      for (; r + 224 < L; r += 256) {
+        double xv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[j] = ldcg(x + r + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int t = 0; t < KP; ++t) acc[t][j & 1] = fma(sV[(r + 32 * j) * KP + t], xv[j], acc[t][j & 1]);
+      }
+      for (; r < L; r += 32) {
+        const double xv = ldcg(x + r);
+#pragma unroll
+        for (int t = 0; t < KP; ++t) acc[t][0] = fma(sV[r * KP + t], xv, acc[t][0]);
+      }
+      double D[KP], E[KP];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) D[t] = warp_sum(acc[t][0] + acc[t][1]);
+#pragma unroll
+      for (int t = 0; t < KP; ++t) {
+        double e2 = 0.0;
+#pragma unroll
+        for (int a = 0; a <= t; ++a) e2 = fma(Tm[a][t], D[a], e2);
+        E[t] = e2;
+      }
+      double nrm0 = 0.0, nrm1 = 0.0;
+      for (int r0 = 0; r0 < L; r0 += 256) {
+        double xv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int rr = r0 + lane + 32 * j;
+          xv[j] = (rr < L) ? ldcg(x + rr) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int rr = r0 + lane + 32 * j;
+          if (rr < L) {
+            double v = xv[j];
+#pragma unroll
+            for (int t = 0; t < KP; ++t) v = fma(-sV[rr * KP + t], E[t], v);
+            x[rr] = v;
+            if (rr >= KP) {
+              if (j & 1) nrm1 = fma(v, v, nrm1);
+              else nrm0 = fma(v, v, nrm0);
+            }
+          }
+        }
+      }
+      const double nrm = warp_sum(nrm0 + nrm1);
+      if (lane == 0 && id >= 0) I.u[id] = sqrt(nrm);
+    }
+  }
+
   // ------------------------------------------------------------ commit
   // Makes J[0:kp] passive: new R columns [W(0:nP, J); R22], the block
   // reflector I - V T^T V^T applied to the trailing rows of every Z column
@@ -1514,6 +1599,17 @@ struct Engine {
     if (tid < kp) s_vt[tid] = ldcg(I.vtop + tid);
     const int nl_share = z_share(s_list, reinterpret_cast<unsigned*>(wk), s_J, kp, true);
     const int nl = nl_share;
+    if (kp <= 4 && L * kp <= WKD) {
+      __syncthreads();  // z_share's scratch in wk is free again
+      switch (kp) {
+        case 1: commit_small<1>(L, wk, s_list, nl); break;
+        case 2: commit_small<2>(L, wk, s_list, nl); break;
+        case 3: commit_small<3>(L, wk, s_list, nl); break;
+        default: commit_small<4>(L, wk, s_list, nl); break;
+      }
+      nP += kp;
+      return sync();
+    }
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
@@ -1624,6 +1720,7 @@ struct Engine {
     }
   }
 
+
   // Deletes position q of R (Algorithm 5 for one column): bookkeeping, the
   // rotation chain over positions q..nP-2 generated in blocks of DB
   // positions (block b on CTA b mod size, handed over through a published
@@ -1681,14 +1778,19 @@ struct Engine {
     }
     if (!sync()) return false;
     phase(PH_CHAIN);
-    // (i) rotation chain on R.  Block b covers generating positions
+    // (i) rotation chain: the rotations only (R's rotated rows are written
+    // with the Z columns in (ii)).  Block b covers generating positions
     // [q + b*DB, q + (b+1)*DB) on CTA b mod size; lane l of warp 0 owns
-    // position bs + l and carries only what the next rotation needs.  Warp 1
-    // publishes the block's rotations to the log as they appear, then
-    // replays them to write the rotated rows of R.
+    // position bs + l.  Warp 0 first carries its columns' running row value
+    // through the earlier blocks' rotations as they appear in the log, then
+    // generates the block's rotations; warp 1 turns them into cosines and
+    // sines and publishes them.  Each warp issues one FP64 instruction per
+    // 64 cycles on its SM sub-partition, so the per-rotation FP64 work on
+    // the dependent chain is kept to two instructions.
     const int nblk = (nrot + DB - 1) / DB;
     double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
-    __shared__ double s_ra[DB], s_ri[DB], s_c0[DB];
+    __shared__ double s_ra[DB];
+    __shared__ int s_rk[DB], s_rid[DB];
     __shared__ int s_prog;  // rotations of the block generated so far (-1: abandoned)
     volatile int* prog = &s_prog;
     for (int blk = tm.rank; blk < nblk; blk += tm.size) {
@@ -1709,11 +1811,12 @@ struct Engine {
       if (warp == 0) {
         const int pl = bs + lane;
         const bool act = pl < np - 1;
-        double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
+        const double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
         double carry = act ? ldcg(col + q) : 0.0;
         // earlier blocks' rotations, as they appear in the log, up to 16 at
         // a time (lanes 0-15 poll cosines, 16-31 sines); the column values
-        // are loaded before the wait
+        // are loaded before the wait.  carry = row t of this column after
+        // rotations q .. t-1: carry' = -sin carry + cos R(t+1, column).
         int t = q;
         bool expired = false;
         const long long tw0 = gtimer();
@@ -1751,10 +1854,7 @@ struct Engine {
           for (int e = 0; e < 16; ++e) {
             if (e < cnt) {
               const double cs = __shfl_sync(0xffffffffu, rv, e), sn = __shfl_sync(0xffffffffu, rv, 16 + e);
-              if (act) {
-                col[t + e] = cs * carry + sn * bot[e];
-                carry = -sn * carry + cs * bot[e];
-              }
+              carry = fma(cs, bot[e], -sn * carry);
             }
           }
           t += cnt;
@@ -1763,52 +1863,123 @@ struct Engine {
           if (lane == 0) *prog = -1;
           continue;
         }
-        s_c0[lane] = carry;
-        // own block: rotation t zeroes R(t+1, position t) = b against
-        // a = R(t, position t).  Every lane forms 1/r = rsqrt(a^2 + b^2) from
-        // the broadcast a, so the dependent chain per position is a shuffle,
-        // an fma, the rsqrt and a multiply; the new row t+1 of lane l is
-        // (a y_l - b x_l)/r.  Only a and 1/r leave the loop.
-        // (the next position's b, b^2 and y are loaded a step ahead)
-        double b = sB[0], y = sB[lane];
-        double bb = b * b;
-        for (t = bs; t < bend; ++t) {
-          const int e = t - bs;
-          const double a = __shfl_sync(0xffffffffu, carry, e);
-          const int en = min(e + 1, DB - 1);
-          const double b_n = sB[en * (DB + 1) + en], y_n = sB[en * (DB + 1) + lane];
-          const double num = fma(a, y, -b * carry);
-          const double r2 = fma(a, a, bb);
-          const bool nz = r2 > 0.0;
-          const double inv = nz ? rsqrt(r2) : 0.0;
-          carry = nz ? inv * num : y;
-          s_ra[e] = a;
-          s_ri[e] = inv;
-          if ((e & 3) == 3 || t == bend - 1) {
-            __threadfence_block();
-            *prog = e + 1;
+        // own block, unnormalised.  Lane l keeps xt_l = X_l S_e, X_l the row
+        // e value of position bs+l, S_e^2 = Q_e the product of the squared
+        // radii of the block's rotations so far (Q_0 = 1).  Rotation e has
+        // a~ = xt of lane e (one shuffle) and b = R(t+1, position t); the new
+        // row e+1 of lane l is a~ y_l - b xt_l at scale S_{e+1}, with
+        // Q_{e+1} = a~^2 + b^2 Q_e formed by the publisher: two FP64
+        // instructions per rotation and no square root or division on the
+        // chain.  Steps run in groups of RG (the group's b and y read from
+        // shared memory first); at a group's end S is renormalised by an exact
+        // power of two if the largest |xt| has left [2^-128, 2^128], and
+        // a~, the zero-radius flags and the exponent go to the publisher.
+        constexpr int RG = 8;
+        double xt = carry;
+        double my_a = 0.0;
+        int my_id = 0;
+        for (int e0 = 0; e0 < nown; e0 += RG) {
+          double bg[RG], yg[RG];
+          int bz = 0;  // bit j: b of step e0+j is zero
+#pragma unroll
+          for (int jj = 0; jj < RG; ++jj) {
+            const int e = min(e0 + jj, DB - 1);
+            bg[jj] = sB[e * (DB + 1) + e];
+            yg[jj] = sB[e * (DB + 1) + lane];
+            bz |= (((unsigned long long)__double_as_longlong(bg[jj]) << 1) == 0ull) ? (1 << jj) : 0;
           }
-          b = b_n;
-          y = y_n;
-          bb = b_n * b_n;
+          const double xt0 = xt;
+          int anyz = 0;
+#pragma unroll
+          for (int jj = 0; jj < RG; ++jj) {
+            const int e = e0 + jj;
+            if (e < nown) {
+              const double nbx = -bg[jj] * xt;
+              const double a = __shfl_sync(0xffffffffu, xt, e);
+              xt = fma(a, yg[jj], nbx);
+              const int az = (((unsigned long long)__double_as_longlong(a) << 1) == 0ull) ? 1 : 0;
+              anyz |= az & (bz >> jj);
+              my_a = (lane == e) ? a : my_a;
+              my_id = (lane == e) ? 0 : my_id;
+            }
+          }
+          if (anyz) {
+            // a zero radius (a~ = b = 0: identity rotation; the rows stay as
+            // they are and the scale restarts at 1): redo the group with it
+            xt = xt0;
+            for (int jj = 0; jj < RG; ++jj) {
+              const int e = e0 + jj;
+              if (e < nown) {
+                const double nbx = -bg[jj] * xt;
+                const double a = __shfl_sync(0xffffffffu, xt, e);
+                const int idr = (a == 0.0 && bg[jj] == 0.0) ? 1 : 0;
+                xt = idr ? yg[jj] : fma(a, yg[jj], nbx);
+                my_a = (lane == e) ? a : my_a;
+                my_id = (lane == e) ? idr : my_id;
+              }
+            }
+          }
+          const int el = min(e0 + RG, nown) - 1;
+          // renormalise S: the largest exponent of the lanes whose row is
+          // still to be generated
+          int ex = (act && lane > el) ? (int)((__double_as_longlong(xt) >> 52) & 0x7ff) : 0;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+          int k = 0;
+          if (ex > 1023 + 128 || (ex > 0 && ex < 1023 - 128)) {
+            k = ex - 1023;
+            xt = ldexp(xt, -k);
+          }
+          if (lane >= e0 && lane <= el) {
+            s_ra[lane] = my_a;
+            s_rid[lane] = my_id;
+            s_rk[lane] = (lane == el) ? k : 0;
+          }
+          __threadfence_block();
+          if (lane == 0) *prog = el + 1;
+          __syncwarp();
         }
       } else if (warp == 1) {
-        // publish (cosine a/r and sine b/r; r = 0 gives the identity)
+        // publish.  Q_{e+1} = (zero radius ? 1 : a~^2 + b^2 Q_e) 2^(-2k_e) is
+        // an affine map of Q_e, so a batch of new rotations (one per lane)
+        // gets its Q values from a warp prefix scan of those maps; then
+        // cos = a~ / S_{e+1}, sin = b S_e / S_{e+1} (identity for a zero
+        // radius).  Batches take whatever the generator has handed over.
         int done = 0;
+        double qrun = 1.0;  // Q_done
         const long long tw0 = gtimer();
         unsigned spins = 0;
-        bool gone = false;
         while (done < nown) {
           const int pg = __shfl_sync(0xffffffffu, *prog, 0);
-          if (pg < 0) { gone = true; break; }
+          if (pg < 0) break;
           if (pg > done) {
             __threadfence_block();
             const int k = done + lane;
-            if (k < pg) {
-              const double a = s_ra[k], inv = s_ri[k], b = sB[k * (DB + 1) + k];
-              I.rots[bs - q + k] = inv != 0.0 ? b * inv : 0.0;
-              I.rotc[bs - q + k] = inv != 0.0 ? a * inv : 1.0;
+            const bool in = k < pg;
+            const double a = in ? s_ra[k] : 0.0, bk = in ? sB[k * (DB + 1) + k] : 0.0;
+            const int idr = in ? s_rid[k] : 0, rk = in ? s_rk[k] : 0;
+            const double sc = (rk != 0) ? ldexp(1.0, -2 * rk) : 1.0;
+            double Cm = in ? (idr ? sc : (a * a) * sc) : 0.0;
+            double Dm = in ? (idr ? 0.0 : (bk * bk) * sc) : 1.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const double Cp = __shfl_up_sync(0xffffffffu, Cm, o);
+              const double Dp = __shfl_up_sync(0xffffffffu, Dm, o);
+              if (lane >= o) {
+                Cm = fma(Dm, Cp, Cm);
+                Dm = Dm * Dp;
+              }
             }
+            const double qnext = fma(Dm, qrun, Cm);  // Q_{k+1}
+            double qk = __shfl_up_sync(0xffffffffu, qnext, 1);
+            if (lane == 0) qk = qrun;                // Q_k
+            if (in) {
+              const double qa = fma(a, a, (bk * bk) * qk);
+              const double iqa = idr ? 0.0 : rsqrt(qa);
+              I.rots[bs - q + k] = idr ? 0.0 : bk * sqrt(qk) * iqa;
+              I.rotc[bs - q + k] = idr ? 1.0 : a * iqa;
+            }
+            qrun = __shfl_sync(0xffffffffu, qnext, pg - done - 1);
             done = pg;
           } else if ((++spins & 63u) == 0u) {
             int bad = 0;
@@ -1820,28 +1991,7 @@ struct Engine {
                 bad = 1;
               }
             }
-            if (__shfl_sync(0xffffffffu, bad, 0)) { gone = true; break; }
-          }
-        }
-        if (!gone) {
-          // replay with the chain's own arithmetic: rows bs .. bend of the
-          // block's columns (the diagonal r, a zero below it)
-          __threadfence_block();
-          const int pl = bs + lane;
-          if (pl < np - 1) {
-            double* col = Rcol(ldcg(I.rslot + pl));
-            double x = s_c0[lane];
-            for (int e = 0; e < nown && e <= lane; ++e) {
-              const double a = s_ra[e], inv = s_ri[e], b = sB[e * (DB + 1) + e];
-              if (e == lane) {
-                col[bs + e] = fma(a, a, b * b) * inv;
-                col[bs + e + 1] = 0.0;
-              } else {
-                const double y = sB[e * (DB + 1) + lane];
-                col[bs + e] = inv != 0.0 ? inv * fma(a, x, b * y) : x;
-                x = inv != 0.0 ? inv * fma(a, y, -b * x) : y;
-              }
-            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) break;
           }
         }
       }
@@ -1849,9 +1999,11 @@ struct Engine {
     if (!sync()) return false;
     phase(PH_ZROT);
     nP = np - 1;
-    // (ii) the same rotations on every Z column and on b: one warp per
-    // column; the carry recurrence c' = -s c + cs * bot is affine, so each
-    // 32-row chunk is a warp-wide prefix scan of affine maps
+    // (ii) the same rotations on every Z column and on b, and on R's columns
+    // at positions q .. nP-1 (rows q .. p+1 of position p take rotations
+    // q .. p; the last one zeroes row p+1): one warp per column; the carry
+    // recurrence c' = -s c + cs * bot is affine, so each 32-row chunk is a
+    // warp-wide prefix scan of affine maps
     {
       double* s_c = dyn;
       double* s_s = dyn + ROT_STAGE;
@@ -1866,6 +2018,9 @@ struct Engine {
         if (ldcg(I.pos + c) < 0) s_zl[atomicAdd(&s_nz, 1)] = c;
       __syncthreads();
       const int nz = s_nz + (do_b ? 1 : 0);
+      int r0, r1;
+      split(nrot, tm.size, tm.rank, r0, r1);
+      const int nunit = nz + (r1 - r0);
       for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
         const int ns = min(ROT_STAGE, nrot - rb);
         __syncthreads();
@@ -1874,15 +2029,26 @@ struct Engine {
           s_s[e] = ldcg(I.rots + rb + e);
         }
         __syncthreads();
-        for (int k = warp; k < nz; k += NW) {
-          double* colp = (k < s_nz) ? Wcol(s_zl[k]) : I.bt;
+        for (int k = warp; k < nunit; k += NW) {
+          double* colp;
+          int nsu = ns;
+          bool rlast = false;  // this chunk ends an R column's rotations
+          if (k < nz) {
+            colp = (k < s_nz) ? Wcol(s_zl[k]) : I.bt;
+          } else {
+            const int pr = q + r0 + (k - nz);  // R column at position pr
+            colp = Rcol(ldcg(I.rslot + pr));
+            nsu = min(ns, pr - q + 1 - rb);
+            if (nsu <= 0) continue;
+            rlast = (rb + nsu == pr - q + 1);
+          }
           double carry = ldcg(colp + q + rb);
           // next chunk's column values are loaded before the scan of this one
-          double nbot = (lane < ns) ? ldcg(colp + q + rb + 1 + lane) : 0.0;
-          for (int t0 = 0; t0 < ns; t0 += 32) {
-            const int cnt = min(32, ns - t0);
+          double nbot = (lane < nsu) ? ldcg(colp + q + rb + 1 + lane) : 0.0;
+          for (int t0 = 0; t0 < nsu; t0 += 32) {
+            const int cnt = min(32, nsu - t0);
             const double bot = nbot;
-            nbot = (t0 + 32 + lane < ns) ? ldcg(colp + q + rb + t0 + 33 + lane) : 0.0;
+            nbot = (t0 + 32 + lane < nsu) ? ldcg(colp + q + rb + t0 + 33 + lane) : 0.0;
             double cs = 1.0, sn = 0.0;
             if (lane < cnt) { cs = s_c[t0 + lane]; sn = s_s[t0 + lane]; }
             double Am = (lane < cnt) ? -sn : 1.0, Bm = (lane < cnt) ? cs * bot : 0.0;
@@ -1901,7 +2067,8 @@ struct Engine {
             if (lane < cnt) colp[q + rb + t0 + lane] = cs * cin + sn * bot;
             carry = __shfl_sync(0xffffffffu, incl, cnt - 1);
           }
-          if (lane == 0) colp[q + rb + ns] = carry;
+          // an R column's last rotation zeroes the entry below its diagonal
+          if (lane == 0) colp[q + rb + nsu] = rlast ? 0.0 : carry;
         }
       }
       // the triangular solve that follows reads rhs = (Q^T b)[0:nP]
