@@ -1783,16 +1783,17 @@ struct Engine {
     // [q + b*DB, q + (b+1)*DB) on CTA b mod size; lane l of warp 0 owns
     // position bs + l.  Warp 0 first carries its columns' running row value
     // through the earlier blocks' rotations as they appear in the log, then
-    // generates the block's rotations; warp 1 turns them into cosines and
-    // sines and publishes them.  Each warp issues one FP64 instruction per
+    // generates the block's rotations; warp 2 forms their scales, warp 1
+    // turns them into cosines and sines and publishes them.  Each warp issues one FP64 instruction per
     // 64 cycles on its SM sub-partition, so the per-rotation FP64 work on
     // the dependent chain is kept to two instructions.
     const int nblk = (nrot + DB - 1) / DB;
     double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
-    __shared__ double s_ra[DB];
+    __shared__ double s_ra[DB], s_rq[DB], s_rqa[DB];
     __shared__ int s_rk[DB], s_rid[DB];
-    __shared__ int s_prog;  // rotations of the block generated so far (-1: abandoned)
+    __shared__ int s_prog, s_qprog;  // rotations generated / with their scale (-1: abandoned)
     volatile int* prog = &s_prog;
+    volatile int* qprog = &s_qprog;
     for (int blk = tm.rank; blk < nblk; blk += tm.size) {
       const int bs = q + blk * DB;
       const int bend = min(bs + DB, np - 1);
@@ -1806,7 +1807,10 @@ struct Engine {
         if (bs + l < np - 1 && e <= l) v = ldcg(Rcol(ldcg(I.rslot + bs + l)) + bs + 1 + e);
         sB[e * (DB + 1) + l] = v;
       }
-      if (tid == 0) *prog = 0;
+      if (tid == 0) {
+        *prog = 0;
+        *qprog = 0;
+      }
       __syncthreads();
       if (warp == 0) {
         const int pl = bs + lane;
@@ -1876,34 +1880,35 @@ struct Engine {
         // a~, the zero-radius flags and the exponent go to the publisher.
         constexpr int RG = 8;
         double xt = carry;
-        double my_a = 0.0;
-        int my_id = 0;
         for (int e0 = 0; e0 < nown; e0 += RG) {
           double bg[RG], yg[RG];
-          int bz = 0;  // bit j: b of step e0+j is zero
 #pragma unroll
           for (int jj = 0; jj < RG; ++jj) {
             const int e = min(e0 + jj, DB - 1);
             bg[jj] = sB[e * (DB + 1) + e];
             yg[jj] = sB[e * (DB + 1) + lane];
-            bz |= (((unsigned long long)__double_as_longlong(bg[jj]) << 1) == 0ull) ? (1 << jj) : 0;
           }
           const double xt0 = xt;
-          int anyz = 0;
+          // lane e stops updating after step e, so at the group's end it
+          // still holds its a~
 #pragma unroll
           for (int jj = 0; jj < RG; ++jj) {
             const int e = e0 + jj;
             if (e < nown) {
               const double nbx = -bg[jj] * xt;
               const double a = __shfl_sync(0xffffffffu, xt, e);
-              xt = fma(a, yg[jj], nbx);
-              const int az = (((unsigned long long)__double_as_longlong(a) << 1) == 0ull) ? 1 : 0;
-              anyz |= az & (bz >> jj);
-              my_a = (lane == e) ? a : my_a;
-              my_id = (lane == e) ? 0 : my_id;
+              if (lane > e) xt = fma(a, yg[jj], nbx);
             }
           }
-          if (anyz) {
+          const int el = min(e0 + RG, nown) - 1;
+          const bool mine = lane >= e0 && lane <= el;
+          double my_b = 0.0;
+#pragma unroll
+          for (int jj = 0; jj < RG; ++jj)
+            if (lane == e0 + jj) my_b = bg[jj];
+          int my_id = 0;
+          const unsigned zm = __ballot_sync(0xffffffffu, mine && xt == 0.0 && my_b == 0.0);
+          if (zm) {
             // a zero radius (a~ = b = 0: identity rotation; the rows stay as
             // they are and the scale restarts at 1): redo the group with it
             xt = xt0;
@@ -1913,13 +1918,15 @@ struct Engine {
                 const double nbx = -bg[jj] * xt;
                 const double a = __shfl_sync(0xffffffffu, xt, e);
                 const int idr = (a == 0.0 && bg[jj] == 0.0) ? 1 : 0;
-                xt = idr ? yg[jj] : fma(a, yg[jj], nbx);
-                my_a = (lane == e) ? a : my_a;
-                my_id = (lane == e) ? idr : my_id;
+                if (lane > e) xt = idr ? yg[jj] : fma(a, yg[jj], nbx);
+                if (lane == e) my_id = idr;
               }
             }
           }
-          const int el = min(e0 + RG, nown) - 1;
+          if (mine) {
+            s_ra[lane] = xt;
+            s_rid[lane] = my_id;
+          }
           // renormalise S: the largest exponent of the lanes whose row is
           // still to be generated
           int ex = (act && lane > el) ? (int)((__double_as_longlong(xt) >> 52) & 0x7ff) : 0;
@@ -1928,41 +1935,41 @@ struct Engine {
           int k = 0;
           if (ex > 1023 + 128 || (ex > 0 && ex < 1023 - 128)) {
             k = ex - 1023;
-            xt = ldexp(xt, -k);
+            if (lane > el) xt = ldexp(xt, -k);
           }
-          if (lane >= e0 && lane <= el) {
-            s_ra[lane] = my_a;
-            s_rid[lane] = my_id;
-            s_rk[lane] = (lane == el) ? k : 0;
-          }
+          if (mine) s_rk[lane] = (lane == el) ? k : 0;
           __threadfence_block();
           if (lane == 0) *prog = el + 1;
           __syncwarp();
         }
-      } else if (warp == 1) {
-        // publish.  Q_{e+1} = (zero radius ? 1 : a~^2 + b^2 Q_e) 2^(-2k_e) is
-        // an affine map of Q_e, so a batch of new rotations (one per lane)
-        // gets its Q values from a warp prefix scan of those maps; then
-        // cos = a~ / S_{e+1}, sin = b S_e / S_{e+1} (identity for a zero
-        // radius).  Batches take whatever the generator has handed over.
+      } else if (warp == 2) {
+        // scale: Q_{e+1} = (zero radius ? 1 : a~^2 + b^2 Q_e) 2^(-2k_e) is an
+        // affine map of Q_e; each group of RG rotations the generator hands
+        // over gets its Q values from a prefix scan of those maps over the
+        // group's lanes (the same association whatever the timing)
+        constexpr int RG = 8;
         int done = 0;
         double qrun = 1.0;  // Q_done
         const long long tw0 = gtimer();
         unsigned spins = 0;
         while (done < nown) {
           const int pg = __shfl_sync(0xffffffffu, *prog, 0);
-          if (pg < 0) break;
-          if (pg > done) {
+          if (pg < 0) {
+            if (lane == 0) *qprog = -1;
+            break;
+          }
+          const int gend = min(done + RG, nown);
+          if (pg >= gend) {
             __threadfence_block();
             const int k = done + lane;
-            const bool in = k < pg;
+            const bool in = k < gend;
             const double a = in ? s_ra[k] : 0.0, bk = in ? sB[k * (DB + 1) + k] : 0.0;
             const int idr = in ? s_rid[k] : 0, rk = in ? s_rk[k] : 0;
             const double sc = (rk != 0) ? ldexp(1.0, -2 * rk) : 1.0;
             double Cm = in ? (idr ? sc : (a * a) * sc) : 0.0;
             double Dm = in ? (idr ? 0.0 : (bk * bk) * sc) : 1.0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
+            for (int o = 1; o < RG; o <<= 1) {
               const double Cp = __shfl_up_sync(0xffffffffu, Cm, o);
               const double Dp = __shfl_up_sync(0xffffffffu, Dm, o);
               if (lane >= o) {
@@ -1974,12 +1981,50 @@ struct Engine {
             double qk = __shfl_up_sync(0xffffffffu, qnext, 1);
             if (lane == 0) qk = qrun;                // Q_k
             if (in) {
-              const double qa = fma(a, a, (bk * bk) * qk);
+              s_rq[k] = qk;
+              s_rqa[k] = idr ? 1.0 : fma(a, a, (bk * bk) * qk);
+            }
+            qrun = __shfl_sync(0xffffffffu, qnext, gend - done - 1);
+            __threadfence_block();
+            if (lane == 0) *qprog = gend;
+            __syncwarp();
+            done = gend;
+          } else if ((++spins & 63u) == 0u) {
+            int bad = 0;
+            if (lane == 0) {
+              int* er = tm_err();
+              bad = (er && *(volatile int*)er) ? 1 : 0;
+              if (!bad && gtimer() - tw0 > WAIT_NS) {
+                if (er) atomicExch(er, 1);
+                bad = 1;
+              }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) {
+              if (lane == 0) *qprog = -1;
+              break;
+            }
+          }
+        }
+      } else if (warp == 1) {
+        // publish cos = a~ / S_{e+1} and sin = b S_e / S_{e+1} (identity for a
+        // zero radius), one rotation per lane, as the scale warp hands them
+        // over
+        int done = 0;
+        const long long tw0 = gtimer();
+        unsigned spins = 0;
+        while (done < nown) {
+          const int pg = __shfl_sync(0xffffffffu, *qprog, 0);
+          if (pg < 0) break;
+          if (pg > done) {
+            __threadfence_block();
+            const int k = done + lane;
+            if (k < pg) {
+              const double a = s_ra[k], bk = sB[k * (DB + 1) + k], qk = s_rq[k], qa = s_rqa[k];
+              const bool idr = s_rid[k] != 0;
               const double iqa = idr ? 0.0 : rsqrt(qa);
               I.rots[bs - q + k] = idr ? 0.0 : bk * sqrt(qk) * iqa;
               I.rotc[bs - q + k] = idr ? 1.0 : a * iqa;
             }
-            qrun = __shfl_sync(0xffffffffu, qnext, pg - done - 1);
             done = pg;
           } else if ((++spins & 63u) == 0u) {
             int bad = 0;
