@@ -34,8 +34,8 @@ constexpr int PW = 2112;             // partial-sum slots per CTA (>= KM(KM+1)/2
 // Slot ranges inside one CTA's partial row.  A range is only rewritten after
 // a barrier that follows every read of its previous contents:
 //   [0, KM(KM+1)/2)        candidate Gram pairs (DM)
-//   [0, 2(KM+1))           panel dots, double-buffered by reflector parity
-//   [2(KM+1), 4(KM+1))     panel pivot row, double-buffered by reflector parity
+//   [0, 8(KM+1))           panel exchange (dots, second dots, two pivot rows),
+//                          double-buffered by exchange parity
 //   [P_O1, P_O1 + 8)       outer-loop argmax / maxima / sums
 //   P_RS                   residual sum of squares
 constexpr int P_O1 = PW - 16;

@@ -614,10 +614,12 @@ struct Engine {
     const int nr = q1 - q0;
     double* sP = dyn;                   // nr x PS: own rows, columns 0..k0 (k0 = Q^T b)
     double* sZ = dyn + PR_MAX * PS;     // KM x KM, rank 0: z_s of reflector i at sZ[s + i KM]
-    double* sG = sZ + KM * KM;          // reduction scratch (NT doubles)
+    double* sG = sZ + KM * KM;          // reduction scratch (2 NT doubles)
+    double* sT = sG + 2 * NT;           // KM x KM, rank 0: T
     __shared__ double s_sum[KM + 1], s_f[KM + 1], s_piv[KM + 1], s_an[KM], s_bt[KM];
-    __shared__ double s_sc[4];          // alpha, v0, beta, sign
-    __shared__ int s_stop;
+    __shared__ double s_k[KM + 1], s_piv2[KM + 1], s_xp[KM + 1], s_A[KM + 1], s_H[KM + 1], s_f2[KM + 1];
+    __shared__ double s_sc[8];          // alpha, v0, beta, sign; the same for the second reflector
+    __shared__ int s_stop, s_stop2;
     for (int e = tid; e < nr * NL; e += NT) {
       const int rr = e / NL, l = e - rr * NL;
       sP[rr * PS + l] = (l < k0) ? ldcg(Wcol(s_J[l]) + nP + q0 + rr) : ldcg(I.bt + nP + q0 + rr);
@@ -639,8 +641,205 @@ struct Engine {
     const int G = NT / NL, gl = tid % NL, gg = tid / NL;
     const bool actg = gg < G;
     int i = 0;
-    for (; i < k0; ++i) {
-      const int pb = (i & 1) * (KM + 1);
+    int step = 0;  // exchanges so far (parity of the partial-sum slots)
+    bool stopped = false;
+    // Reflectors two at a time, one exchange for both.  With x the columns
+    // before reflector i (rows > i), the exchange carries G_l = x_i^T x_l
+    // (rows > i), K_l = x_{i+1}^T x_l (rows > i+1) and pivot rows i and
+    // i+1.  Reflector i is formed as in the single step; then, with
+    // A_l = x_i^T x_l and B = x_i^T x_i over rows > i+1, the columns after
+    // reflector i satisfy x'_{i+1}^T x'_l = K_l - f_l A_{i+1} - f_{i+1} A_l
+    // + f_{i+1} f_l B (A_{i+1} = K_i) and x'_l[i+1] = x_l[i+1] - f_l x_i[i+1],
+    // which is all reflector i+1 needs.  Exact in exact arithmetic; the
+    // rounding is of the order of the direct dots'.
+    for (; i + 1 < k0; i += 2) {
+      const int pb = (step & 1) * 4 * (KM + 1);
+      ++step;
+      double* mypart = I.part + (size_t)tm.rank * PW;
+      const int r0 = max(q0, i + 1) - q0, r1 = max(q0, i + 2) - q0;
+      {
+        double sg_ = 0.0, sk_ = 0.0;
+        if (actg) {
+          for (int rr = r0 + gg; rr < nr; rr += G) {
+            const double xl = sP[rr * PS + gl];
+            sg_ = fma(xl, sP[rr * PS + i], sg_);
+            if (rr >= r1) sk_ = fma(xl, sP[rr * PS + i + 1], sk_);
+          }
+          sG[gg * NL + gl] = sg_;
+          sG[NT + gg * NL + gl] = sk_;
+        }
+        __syncthreads();
+        for (int st = 1; st < G; st <<= 1) {
+          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) {
+            sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
+            sG[NT + gg * NL + gl] += sG[NT + (gg + st) * NL + gl];
+          }
+          __syncthreads();
+        }
+        if (tid <= k0) {
+          mypart[pb + tid] = sG[tid];
+          mypart[pb + (KM + 1) + tid] = sG[NT + tid];
+        }
+      }
+      if (i >= q0 && i < q1 && tid <= k0) mypart[pb + 2 * (KM + 1) + tid] = sP[(i - q0) * PS + tid];
+      if (i + 1 >= q0 && i + 1 < q1 && tid <= k0) mypart[pb + 3 * (KM + 1) + tid] = sP[(i + 1 - q0) * PS + tid];
+      if (!sync()) return false;
+      {
+        const int own = owner(i), own2 = owner(i + 1);
+        if (tid <= k0) {
+          s_piv[tid] = ldcg(I.part + (size_t)own * PW + pb + 2 * (KM + 1) + tid);
+          s_piv2[tid] = ldcg(I.part + (size_t)own2 * PW + pb + 3 * (KM + 1) + tid);
+        }
+        if (actg) {
+          const int cnt = (tm.size - gg + G - 1) / G;
+          double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
+          for (int j0 = 0; j0 < cnt; j0 += 2) {
+            const size_t o0 = (size_t)(gg + j0 * G) * PW + pb + gl;
+            const double v0 = ldcg(I.part + o0), w0 = ldcg(I.part + o0 + (KM + 1));
+            double v1 = 0.0, w1 = 0.0;
+            if (j0 + 1 < cnt) {
+              const size_t o1 = (size_t)(gg + (j0 + 1) * G) * PW + pb + gl;
+              v1 = ldcg(I.part + o1);
+              w1 = ldcg(I.part + o1 + (KM + 1));
+            }
+            a0 += v0;
+            c0 += w0;
+            if (j0 + 1 < cnt) {
+              a1 += v1;
+              c1 += w1;
+            }
+          }
+          sG[gg * NL + gl] = a0 + a1;
+          sG[NT + gg * NL + gl] = c0 + c1;
+        }
+        __syncthreads();
+        for (int st = 1; st < G; st <<= 1) {
+          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) {
+            sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
+            sG[NT + gg * NL + gl] += sG[NT + (gg + st) * NL + gl];
+          }
+          __syncthreads();
+        }
+      }
+      // reflector i
+      if (warp == 0 && lane == 0) {
+        const double xii = s_piv[i], ssum_i = sG[i];
+        const double alpha = sqrt(fma(xii, xii, ssum_i));
+        const int stop = (i >= L || !(alpha > (100.0 * EPS) * s_an[i])) ? 1 : 0;
+        const double sg = (xii >= 0.0) ? 1.0 : -1.0;
+        const double v0 = xii + sg * alpha;
+        s_stop = stop;
+        s_sc[0] = alpha;
+        s_sc[1] = v0;
+        s_sc[2] = stop ? 0.0 : 2.0 / fma(v0, v0, ssum_i);
+        s_sc[3] = sg;
+      }
+      __syncthreads();
+      if (s_stop) {
+        stopped = true;
+        break;
+      }
+      const double v0 = s_sc[1], beta = s_sc[2];
+      if (tid <= k0) {
+        const double gs = sG[tid], ks = sG[NT + tid];
+        s_sum[tid] = gs;
+        s_k[tid] = ks;
+        const double f = (tid > i) ? beta * fma(v0, s_piv[tid], gs) : 0.0;
+        s_f[tid] = f;
+        // row i+1 after reflector i, and A_l over rows > i+1
+        s_xp[tid] = fma(-f, s_piv2[i], s_piv2[tid]);
+        s_A[tid] = fma(-s_piv2[i], s_piv2[tid], gs);
+      }
+      __syncthreads();
+      if (tid <= k0) {
+        const double fi1 = s_f[i + 1], Ai1 = s_k[i];
+        const double Bq = fma(-s_piv2[i], s_piv2[i], s_sum[i]);
+        const double fl = s_f[tid];
+        double h = fma(-fl, Ai1, s_k[tid]);
+        h = fma(-fi1, s_A[tid], h);
+        h = fma(fi1 * fl, Bq, h);
+        s_H[tid] = h;
+      }
+      __syncthreads();
+      // reflector i+1 on the columns after reflector i
+      if (warp == 0 && lane == 0) {
+        const double xii = s_xp[i + 1], ssum_i = s_H[i + 1];
+        const double alpha = sqrt(fma(xii, xii, ssum_i));
+        const int stop = (i + 1 >= L || !(alpha > (100.0 * EPS) * s_an[i + 1])) ? 1 : 0;
+        const double sg = (xii >= 0.0) ? 1.0 : -1.0;
+        const double v0b = xii + sg * alpha;
+        s_stop2 = stop;
+        s_sc[4] = alpha;
+        s_sc[5] = v0b;
+        s_sc[6] = stop ? 0.0 : 2.0 / fma(v0b, v0b, ssum_i);
+        s_sc[7] = sg;
+      }
+      __syncthreads();
+      const bool two = !s_stop2;
+      const double v0b = s_sc[5], beta2 = s_sc[6];
+      if (tid <= k0) {
+        s_f2[tid] = (two && tid > i + 1) ? beta2 * fma(v0b, s_xp[tid], s_H[tid]) : 0.0;
+        if (tm.rank == 0 && tid < i) sZ[tid + i * KM] = fma(s_piv[tid], v0, s_sum[tid]);  // z_s = v_s^T v_i
+        if (tm.rank == 0 && two && tid <= i) {
+          // z_s = v_s^T v_{i+1}: v_s[i+1] v0' + x_s^T x'_{i+1} over rows > i+1
+          const double xs_x = (tid == i) ? fma(-s_f[i + 1], fma(-s_piv2[i], s_piv2[i], s_sum[i]), s_k[i])
+                                         : fma(-s_f[i + 1], s_A[tid], s_k[tid]);
+          sZ[tid + (i + 1) * KM] = fma(s_piv2[tid], v0b, xs_x);
+        }
+      }
+      __syncthreads();
+      if (tm.rank == 0) {
+        if (tid == i) I.R22[i + i * KM] = -s_sc[3] * s_sc[0];
+        if (tid > i && tid < k0) I.R22[i + tid * KM] = s_piv[tid] - s_f[tid] * v0;
+        if (tid == k0) I.pr[i] = s_piv[k0] - s_f[k0] * v0;
+        if (tid == 0) {
+          I.vtop[i] = v0;
+          I.beta[i] = beta;
+          s_bt[i] = beta;
+        }
+        if (two) {
+          if (tid == i + 1) I.R22[(i + 1) + (i + 1) * KM] = -s_sc[7] * s_sc[4];
+          if (tid > i + 1 && tid < k0) I.R22[(i + 1) + tid * KM] = s_xp[tid] - s_f2[tid] * v0b;
+          if (tid == k0) I.pr[i + 1] = s_xp[k0] - s_f2[k0] * v0b;
+          if (tid == 0) {
+            I.vtop[i + 1] = v0b;
+            I.beta[i + 1] = beta2;
+            s_bt[i + 1] = beta2;
+          }
+        }
+      }
+      flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i) + 1) * (double)(L - i));
+      if (two) flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i - 1) + 1) * (double)(L - i - 1));
+      // own rows: reflector i on rows > i (columns > i), then reflector i+1
+      // on rows > i+1 (columns > i+1); the row's column i+1 after reflector
+      // i is recomputed per element
+      // (columns i+2 .. first, reading column i+1 before it is updated)
+      {
+        const int nl = k0 - i - 1;
+        for (int e = tid; e < (nr - r0) * nl; e += NT) {
+          const int rr = r0 + e / nl, l = i + 2 + (e - (e / nl) * nl);
+          const double xi = sP[rr * PS + i];
+          double x = fma(-s_f[l], xi, sP[rr * PS + l]);
+          if (two && rr >= r1) {
+            const double xi1 = fma(-s_f[i + 1], xi, sP[rr * PS + i + 1]);
+            x = fma(-s_f2[l], xi1, x);
+          }
+          sP[rr * PS + l] = x;
+        }
+      }
+      __syncthreads();
+      for (int rr = r0 + tid; rr < nr; rr += NT)
+        sP[rr * PS + i + 1] = fma(-s_f[i + 1], sP[rr * PS + i], sP[rr * PS + i + 1]);
+      __syncthreads();
+      if (!two) {
+        i += 1;
+        stopped = true;
+        break;
+      }
+    }
+    for (; i < k0 && !stopped; ++i) {
+      const int pb = (step & 1) * 4 * (KM + 1);
+      ++step;
       double* mypart = I.part + (size_t)tm.rank * PW;
       // dots of column i with every column (and Q^T b) over own rows > i:
       // rows r0 + gg, r0 + gg + G, ... per thread, then a pairwise tree
@@ -739,8 +938,7 @@ struct Engine {
     }
     if (tm.rank == 0) {
       // T column by column: T[c, c] = beta_c, T[0:c, c] = -beta_c T[0:c, 0:c] z_c
-      // (thread r computes row r; sG holds T column-major with stride KM)
-      double* sT = sG + NT;  // KM x KM, column-major
+      // (thread r computes row r; sT column-major with stride KM)
       for (int c = 0; c < kk; ++c) {
         if (tid < c) {
           double c0 = 0.0, c1 = 0.0;
