@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "lhdm.h"
@@ -105,6 +106,8 @@ struct Inst {
   double* accb;   // ceil(cap/TB) x TB slab accumulations of the pipelined solve
   int* tflag;     // ceil(cap/TB) block flags, ceil(cap/TB) * TB/SLAB slab flags, ceil(cap/TB) * INV_PARTS inverse flags
   unsigned long long* amask;  // KM acceptance masks
+  unsigned* Vd;   // panel reflectors as 7-bit digits: ND x m rows x 16 words (bf16 pairs), null: none
+  int* Ver;       // m: row scale exponents of Vd (|V(r, :)| < 2^Ver[r])
   double* phase_ns;           // NPHASE (may be null)
   int* trace;                 // 6 ints per outer step (may be null)
   int trace_cap;              // rows available in trace
@@ -204,6 +207,90 @@ __device__ __forceinline__ int block_sum_int(int v, int* sh) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   return t;
+}
+
+// ------------------------------------------- FP64 products on bf16 MMA
+// A double x with |x| < 2^E is held as the fixed-point integer
+// Y = round(|x| 2^(56-E)) < 2^56, cut into ND = 8 digits of 7 bits
+// (Y = sum_k d_k 2^(49-7k)), each exactly a bf16 (sign of x).  A product
+// of digits is below 2^14, so sums of up to 2^10 of them are exact in the
+// FP32 accumulators of the tensor cores.  A dot product is rebuilt from its
+// level sums P_lam = sum_{k+l=lam} (digit-pair sums) as
+// sum_lam 2^(-7 lam) P_lam over the levels lam <= NLV-1 = 8; the pairs left
+// out carry weight below 2^-59 of the operands' scales, so the result is as
+// accurate as a dot product in FP64.
+constexpr int ND = 8;
+constexpr int NLV = ND + 1;
+
+// round(|x| 2^sh) for |x| 2^sh < 2^56 (zero and subnormal x give 0).  Only
+// elements at least 2^3 below the scale are rounded, so the result stays
+// below 2^56.
+__device__ __forceinline__ unsigned long long fix56(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFu);
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  const int s = e - 1075 + sh;
+  unsigned long long y = 0ull;
+  if (s >= 0) y = mant << (s > 3 ? 3 : s);
+  else if (s > -64) y = (mant + (1ull << (-s - 1))) >> (-s);
+  return e == 0 ? 0ull : y;
+}
+// exponent bound: |x| < 2^ebound(x); -2000 for zero and subnormals
+__device__ __forceinline__ int ebound(double x) {
+  const int e = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu);
+  return e == 0 ? -2000 : e - 1022;
+}
+// Y as two 28-bit halves (digits 0-3 in hi, 4-7 in lo)
+__device__ __forceinline__ void halves28(unsigned long long y, unsigned& hi, unsigned& lo) {
+  hi = (unsigned)(y >> 28);
+  lo = (unsigned)y & 0x0FFFFFFFu;
+}
+// sign words of two values for dig2: (+-1, +-1) and (-+128, -+128) as bf16x2
+__device__ __forceinline__ void sign2(bool nega, bool negb, unsigned& sg, unsigned& nb) {
+  sg = (nega ? 0xBF80u : 0x3F80u) | ((negb ? 0xBF80u : 0x3F80u) << 16);
+  nb = (nega ? 0x4300u : 0xC300u) | ((negb ? 0x4300u : 0xC300u) << 16);
+}
+// digit at bit offset sh of two half-words as bf16x2 (a low, b high):
+// bf16 0x4300 | d is 128 + d, and s (128 + d) - 128 s = s d exactly
+__device__ __forceinline__ unsigned dig2(unsigned wa, unsigned wb, int sh, unsigned sg, unsigned nb) {
+  const unsigned p = ((wa >> sh) & 0x7Fu) | (((wb >> sh) & 0x7Fu) << 16) | 0x43004300u;
+  unsigned r;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(p), "r"(sg), "r"(nb));
+  return r;
+}
+// digit k (0..7) of a value given as 28-bit halves
+__device__ __forceinline__ unsigned dig2k(int k, unsigned ha, unsigned la, unsigned hb, unsigned lb, unsigned sg,
+                                          unsigned nb) {
+  const int sh = 21 - 7 * (k & 3);
+  return k < 4 ? dig2(ha, hb, sh, sg, nb) : dig2(la, lb, sh, sg, nb);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ldsm_x4(unsigned* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_u32(p)));
+}
+// c += a b, m16n8k16, bf16 in, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// 2^e as a double (normal range) or via ldexp
+__device__ __forceinline__ double pow2d(int e) {
+  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
 }
 
 // ---------------------------------------------------------------- teams

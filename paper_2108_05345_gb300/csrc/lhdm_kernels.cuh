@@ -41,7 +41,8 @@ struct ScratchLayout {
   size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, candw, rotc, rots, apu;
   size_t Dinv, accb;  // pipelined triangular solve (teams of more than one CTA)
   size_t dtotal;
-  size_t pos, J, candi, candn, ipart, ctl, qlist, tflag;
+  size_t Vd;  // reflector digits (teams of more than one CTA)
+  size_t pos, J, candi, candn, ipart, ctl, qlist, tflag, Ver;
   size_t itotal;
   int ldw;
   bool pipelined;
@@ -81,6 +82,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.pipelined = team > 1;
   L.Dinv = take(L.pipelined ? nbk * TB * TB : 1);
   L.accb = take(L.pipelined ? nbk * TB : 1);
+  L.Vd = take(L.pipelined ? (size_t)ND * m * 8 : 1);  // ND x m x 16 words
   L.dtotal = o;
   o = 0;
   L.pos = take(n);
@@ -91,6 +93,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.ctl = take(16);
   L.qlist = take(cap);
   L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB + INV_PARTS) : 1);
+  L.Ver = take(L.pipelined ? m : 1);
   L.itotal = o;
   return L;
 }
@@ -126,6 +129,8 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.Dinv = L.pipelined ? d + L.Dinv : nullptr;
   I.accb = L.pipelined ? d + L.accb : nullptr;
   I.tflag = L.pipelined ? ip + L.tflag : nullptr;
+  I.Vd = L.pipelined ? reinterpret_cast<unsigned*>(d + L.Vd) : nullptr;
+  I.Ver = L.pipelined ? ip + L.Ver : nullptr;
   I.amask = nullptr;
 }
 

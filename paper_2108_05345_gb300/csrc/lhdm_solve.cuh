@@ -37,6 +37,7 @@ struct Engine {
   int nonfinite = 0;
   bool u_dirty = false;
   bool failed = false;
+  bool vd_ok = false;  // the current panel's reflector digits are in Vd/Ver
   int kdm = 0, removed = 0, inner_step = 0;
   int inv_valid = 0;  // positions whose diagonal-block inverse column is current
   int tepoch = 0;     // pipelined-solve calls in this launch (flag values)
@@ -488,6 +489,7 @@ struct Engine {
   // the compact WY form accumulated alongside.  Rows are split over CTAs;
   // each reflector costs one team barrier.
   __device__ bool panel(const int* s_J) {
+    vd_ok = false;
     const int L = I.m - nP;
     if (kk > L) kk = L;
     int q0, q1;
@@ -605,6 +607,7 @@ struct Engine {
   // (FP64 issue is the scarce resource here: every warp instruction counts.)
   static constexpr int PR_MAX = 64;
   static constexpr int PS = KM + 1;  // row stride of the staged panel
+  static constexpr int RED_U = 12;   // partial-sum loads in flight per thread
   __device__ bool panel_smem(const int* s_J) {
     const int L = I.m - nP;
     if (kk > L) kk = L;
@@ -619,6 +622,7 @@ struct Engine {
     __shared__ double s_sum[KM + 1], s_f[KM + 1], s_piv[KM + 1], s_an[KM], s_bt[KM];
     __shared__ double s_k[KM + 1], s_piv2[KM + 1], s_xp[KM + 1], s_A[KM + 1], s_H[KM + 1], s_f2[KM + 1];
     __shared__ double s_sc[8];          // alpha, v0, beta, sign; the same for the second reflector
+    __shared__ double s_v0[KM];         // v0 of every reflector (every CTA)
     __shared__ int s_stop, s_stop2;
     for (int e = tid; e < nr * NL; e += NT) {
       const int rr = e / NL, l = e - rr * NL;
@@ -691,22 +695,27 @@ struct Engine {
           s_piv2[tid] = ldcg(I.part + (size_t)own2 * PW + pb + 3 * (KM + 1) + tid);
         }
         if (actg) {
+          // ranks gg, gg + G, ...: every load of a round in flight at once
           const int cnt = (tm.size - gg + G - 1) / G;
           double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
-          for (int j0 = 0; j0 < cnt; j0 += 2) {
-            const size_t o0 = (size_t)(gg + j0 * G) * PW + pb + gl;
-            const double v0 = ldcg(I.part + o0), w0 = ldcg(I.part + o0 + (KM + 1));
-            double v1 = 0.0, w1 = 0.0;
-            if (j0 + 1 < cnt) {
-              const size_t o1 = (size_t)(gg + (j0 + 1) * G) * PW + pb + gl;
-              v1 = ldcg(I.part + o1);
-              w1 = ldcg(I.part + o1 + (KM + 1));
+          for (int j0 = 0; j0 < cnt; j0 += RED_U) {
+            double v[RED_U], w[RED_U];
+#pragma unroll
+            for (int k = 0; k < RED_U; ++k) {
+              const size_t o = (size_t)(gg + (j0 + k) * G) * PW + pb + gl;
+              v[k] = (j0 + k < cnt) ? ldcg(I.part + o) : 0.0;
+              w[k] = (j0 + k < cnt) ? ldcg(I.part + o + (KM + 1)) : 0.0;
             }
-            a0 += v0;
-            c0 += w0;
-            if (j0 + 1 < cnt) {
-              a1 += v1;
-              c1 += w1;
+#pragma unroll
+            for (int k = 0; k < RED_U; k += 2) {
+              if (j0 + k < cnt) {
+                a0 += v[k];
+                c0 += w[k];
+              }
+              if (j0 + k + 1 < cnt) {
+                a1 += v[k + 1];
+                c1 += w[k + 1];
+              }
             }
           }
           sG[gg * NL + gl] = a0 + a1;
@@ -740,6 +749,7 @@ struct Engine {
         break;
       }
       const double v0 = s_sc[1], beta = s_sc[2];
+      if (tid == 0) s_v0[i] = v0;
       if (tid <= k0) {
         const double gs = sG[tid], ks = sG[NT + tid];
         s_sum[tid] = gs;
@@ -777,6 +787,7 @@ struct Engine {
       __syncthreads();
       const bool two = !s_stop2;
       const double v0b = s_sc[5], beta2 = s_sc[6];
+      if (tid == 0 && two) s_v0[i + 1] = v0b;
       if (tid <= k0) {
         s_f2[tid] = (two && tid > i + 1) ? beta2 * fma(v0b, s_xp[tid], s_H[tid]) : 0.0;
         if (tm.rank == 0 && tid < i) sZ[tid + i * KM] = fma(s_piv[tid], v0, s_sum[tid]);  // z_s = v_s^T v_i
@@ -867,15 +878,16 @@ struct Engine {
         if (actg) {
           const int cnt = (tm.size - gg + G - 1) / G;
           double a0 = 0.0, a1 = 0.0;
-          for (int j0 = 0; j0 < cnt; j0 += 4) {
-            double v[4];
+          for (int j0 = 0; j0 < cnt; j0 += RED_U) {
+            double v[RED_U];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < RED_U; ++k)
               v[k] = (j0 + k < cnt) ? ldcg(I.part + (size_t)(gg + (j0 + k) * G) * PW + pb + gl) : 0.0;
-            a0 += v[0];
-            if (j0 + 1 < cnt) a1 += v[1];
-            if (j0 + 2 < cnt) a0 += v[2];
-            if (j0 + 3 < cnt) a1 += v[3];
+#pragma unroll
+            for (int k = 0; k < RED_U; k += 2) {
+              if (j0 + k < cnt) a0 += v[k];
+              if (j0 + k + 1 < cnt) a1 += v[k + 1];
+            }
           }
           sG[gg * NL + gl] = a0 + a1;
         }
@@ -904,6 +916,7 @@ struct Engine {
       __syncthreads();
       if (s_stop) break;
       const double v0 = s_sc[1], beta = s_sc[2];
+      if (tid == 0) s_v0[i] = v0;
       if (tid <= k0) {
         const double ssum = sG[tid];
         s_sum[tid] = ssum;
@@ -936,23 +949,49 @@ struct Engine {
       const int rr = e / kk, t = e - rr * kk;
       I.V[(size_t)(q0 + rr) * KM + t] = sP[rr * PS + t];
     }
-    if (tm.rank == 0) {
-      // T column by column: T[c, c] = beta_c, T[0:c, c] = -beta_c T[0:c, 0:c] z_c
-      // (thread r computes row r; sT column-major with stride KM)
-      for (int c = 0; c < kk; ++c) {
-        if (tid < c) {
-          double c0 = 0.0, c1 = 0.0;
-          int sidx = tid;
-          for (; sidx + 1 < c; sidx += 2) {
-            c0 = fma(sT[tid + sidx * KM], sZ[sidx + c * KM], c0);
-            c1 = fma(sT[tid + (sidx + 1) * KM], sZ[sidx + 1 + c * KM], c1);
-          }
-          if (sidx < c) c0 = fma(sT[tid + sidx * KM], sZ[sidx + c * KM], c0);
-          sT[tid + c * KM] = -s_bt[c] * (c0 + c1);
+    // the same rows as 7-bit digits for the tensor-core commit: one warp per
+    // row, lane t holds V(row, t) (v0 on the diagonal, zero above), the row
+    // scale is its largest exponent bound, and even lanes store digit pairs
+    vd_ok = I.Vd != nullptr && kk > 4 && kk <= 32;
+    if (vd_ok) {
+      for (int rr = warp; rr < nr; rr += NW) {
+        const int row = q0 + rr;
+        const double v = (lane < kk) ? (row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0)) : 0.0;
+        const int er = __reduce_max_sync(0xffffffffu, ebound(v));
+        unsigned ha, la;
+        halves28(fix56(v, 56 - er), ha, la);
+        const unsigned hb = __shfl_down_sync(0xffffffffu, ha, 1), lb = __shfl_down_sync(0xffffffffu, la, 1);
+        const bool nega = v < 0.0;
+        const bool negb = __shfl_down_sync(0xffffffffu, nega ? 1 : 0, 1) != 0;
+        unsigned sg, nb2;
+        sign2(nega, negb, sg, nb2);
+        if ((lane & 1) == 0) {
+#pragma unroll
+          for (int k = 0; k < ND; ++k) I.Vd[((size_t)k * I.m + row) * 16 + (lane >> 1)] = dig2k(k, ha, la, hb, lb, sg, nb2);
         }
-        if (tid == c) sT[c + c * KM] = s_bt[c];
-        __syncthreads();
+        if (lane == 0) I.Ver[row] = er;
       }
+    }
+    if (tm.rank == 0) {
+      // T is the inverse of the upper triangle M with M[r][r] = 1/beta_r and
+      // M[r][s] = z_rs = v_r^T v_s (r < s).  Column c by back substitution on
+      // one warp, all columns at once: x[c] = beta_c, then for s = c .. 1 the
+      // lanes add z_rs x[s] into row r < s and x[s-1] = -beta_{s-1} acc[s-1]
+      // (lane r holds rows r and r + 32; sT column-major with stride KM).
+      for (int c = warp; c < kk; c += NW) {
+        double acc0 = 0.0, acc1 = 0.0;
+        double xs = s_bt[c];
+        if (lane == 0) sT[c + c * KM] = xs;
+        for (int sidx = c; sidx >= 1; --sidx) {
+          if (lane < sidx) acc0 = fma(sZ[lane + sidx * KM], xs, acc0);
+          if (lane + 32 < sidx) acc1 = fma(sZ[lane + 32 + sidx * KM], xs, acc1);
+          const int r = sidx - 1;
+          const double a = __shfl_sync(0xffffffffu, r < 32 ? acc0 : acc1, r & 31);
+          xs = -s_bt[r] * a;
+          if (lane == 0) sT[r + c * KM] = xs;
+        }
+      }
+      __syncthreads();
       for (int e = tid; e < kk * kk; e += NT) {
         const int c = e / kk, r = e - c * kk;
         if (r <= c) I.T[r + c * KM] = sT[r + c * KM];
@@ -1658,6 +1697,248 @@ struct Engine {
     }
   }
 
+  // One batch of nb <= NBP (8 or 16) columns through the bf16 tensor cores,
+  // for 5 <= kp <= 32 with the panel's reflector digits in Vd/Ver.
+  //  pass 1: D = V^T C.  With V(r, :) = 2^Er v'(r, :) (|v'| < 1, digits a_k
+  //    from the panel) and C' = 2^Er C (digits c_l under the column scale
+  //    2^Ec), D = 2^(Ec-14) sum_lam 2^(-7 lam) sum_{k+l=lam} a_k^T c_l.  Warp
+  //    (combo, sub) takes rows sub*16 .. +15 of every chunk for one 16 x 8
+  //    (reflector, column) tile and keeps one FP32 accumulator per level
+  //    k + l, moved to int32 every 128 of its rows (exact: at most 8 pairs of
+  //    products below 2^14 per row).
+  //  D' = T^T D in FP64.
+  //  pass 2: C -= V D'.  From the digits of V (row scale) and of D' (column
+  //    scale 2^Ee) warp (row tile, column tile) forms the 9 level sums of its
+  //    16 x 8 tile (exact in FP32: at most 8 pairs x 32 terms), combines them
+  //    in int64 (u = sum_lam lev_lam 2^(43-7 lam), levels 7 and 8 rounded
+  //    down; |u| < 2^63 as lev_lam < (lam+1) 2^19) and applies
+  //    x -= u 2^(Er+Ee-57) and the trailing norm in FP64.
+  // Every sum is exact or in a fixed order, so the result is bitwise
+  // reproducible.
+  template <int NBP>
+  __device__ void commit_tc(const CommitShape& cs, int nb) {
+    constexpr int NTN = NBP / 8;           // column tiles
+    constexpr int COMBOS = 2 * NTN;        // (reflector tile, column tile) pairs
+    constexpr int SUB = NW / COMBOS;       // pass-1 warps per pair
+    constexpr int R1 = 16 * SUB;           // pass-1 rows per chunk (64 or 128)
+    constexpr int R2 = 128;                // pass-2 rows per chunk
+    constexpr int RMAX = 128;
+    constexpr int SA = 40;                 // row stride of staged V digits (bf16)
+    constexpr int SB = R1 + 8;             // row stride of C' digits (bf16)
+    constexpr int SE = 40;                 // row stride of D' digits (bf16)
+    const int L = cs.L;
+    unsigned short* sA = reinterpret_cast<unsigned short*>(cs.wk);  // ND x RMAX x SA
+    unsigned short* sB = sA + ND * RMAX * SA;                         // ND x NBP x SB
+    int* sEr = reinterpret_cast<int*>(sB + ND * NBP * SB);           // RMAX row exponents
+    __shared__ int s_Ec[CB], s_Ee[CB];
+    const int g = lane >> 2, tq = lane & 3;
+    // V digits of rows rb .. rb+R (zero past L) and their row exponents
+    auto stage = [&](int rb, int R) {
+      const int nr = min(R, L - rb);
+      for (int e = tid; e < ND * R * 4; e += NT) {
+        const int k = e / (R * 4), rem = e - k * (R * 4), rr = rem >> 2, q = rem & 3;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (rr < nr) v = __ldcg(reinterpret_cast<const uint4*>(I.Vd + ((size_t)k * I.m + rb + rr) * 16) + q);
+        *reinterpret_cast<uint4*>(sA + (k * RMAX + rr) * SA + q * 8) = v;
+      }
+      if (tid < R) sEr[tid] = (tid < nr) ? ldcg(I.Ver + rb + tid) : 0;
+    };
+    // column scales of C' = 2^Er C
+    for (int c = warp; c < nb; c += NW) {
+      const double* col = commit_col(cs.s_cid, c);
+      int mx = -8000;
+      for (int r = lane; r < L; r += 32) {
+        const int e = ebound(ldcg(col + r));
+        if (e > -2000) mx = max(mx, e + ldcg(I.Ver + r));
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) s_Ec[c] = mx;
+    }
+    // ---- pass 1
+    const int cmb = warp % COMBOS, sub = warp / COMBOS;
+    const int mt = cmb & 1, nt = cmb >> 1;
+    float acc[NLV][4];
+    int iacc[NLV][4];
+#pragma unroll
+    for (int l = 0; l < NLV; ++l)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[l][j] = 0.f;
+        iacc[l][j] = 0;
+      }
+    int since = 0;
+    for (int rb = 0; rb < L; rb += R1) {
+      const int nr = min(R1, L - rb);
+      __syncthreads();
+      stage(rb, R1);
+      __syncthreads();
+      // digits of C': thread (column, row pair), one bf16 pair per digit
+      for (int e = tid; e < NBP * (R1 / 2); e += NT) {
+        const int c = e / (R1 / 2), rr = 2 * (e - c * (R1 / 2));
+        unsigned w[ND];
+        if (c < nb) {
+          const double* col = commit_col(cs.s_cid, c) + rb;
+          const double xa = (rr < nr) ? ldcg(col + rr) : 0.0;
+          const double xb = (rr + 1 < nr) ? ldcg(col + rr + 1) : 0.0;
+          const int ec = s_Ec[c];
+          unsigned ha, la, hb, lb, sg, nb2;
+          halves28(fix56(xa, sEr[rr] + 56 - ec), ha, la);
+          halves28(fix56(xb, sEr[rr + 1] + 56 - ec), hb, lb);
+          sign2(xa < 0.0, xb < 0.0, sg, nb2);
+#pragma unroll
+          for (int k = 0; k < ND; ++k) w[k] = dig2k(k, ha, la, hb, lb, sg, nb2);
+        } else {
+#pragma unroll
+          for (int k = 0; k < ND; ++k) w[k] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sB + (k * NBP + c) * SB + rr) = w[k];
+      }
+      __syncthreads();
+      {
+        const int r0 = sub * 16;
+        unsigned bq[ND][2];
+#pragma unroll
+        for (int l = 0; l < ND; ++l) ldsm_x2(bq[l], sB + (l * NBP + nt * 8 + (lane & 7)) * SB + r0 + ((lane >> 3) & 1) * 8);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+          unsigned a[4];
+          ldsm_x4_t(a, sA + (k * RMAX + r0 + (lane & 7) + ((lane >> 4) << 3)) * SA + mt * 16 + ((lane >> 3) & 1) * 8);
+#pragma unroll
+          for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(acc[k + l], a, bq[l]);
+        }
+      }
+      since += 16;
+      if (since == 128 || rb + R1 >= L) {
+#pragma unroll
+        for (int l = 0; l < NLV; ++l)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            iacc[l][j] += __float2int_rn(acc[l][j]);
+            acc[l][j] = 0.f;
+          }
+        since = 0;
+      }
+    }
+    // sum over the sub-blocks (exact, int64) and D from the level sums
+    __syncthreads();
+    int* sStage = reinterpret_cast<int*>(sA);                             // NW x NLV x 32 x 4 (72 KB)
+    double* sL = reinterpret_cast<double*>(reinterpret_cast<char*>(sA) + 73728);  // NLV x 32 x NBP
+#pragma unroll
+    for (int l = 0; l < NLV; ++l)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sStage[((warp * NLV + l) * 32 + lane) * 4 + j] = iacc[l][j];
+    __syncthreads();
+    for (int e = tid; e < COMBOS * NLV * 128; e += NT) {
+      const int j = e & 3, ln = (e >> 2) & 31, lam = (e >> 7) % NLV, cb = (e >> 7) / NLV;
+      long long v = 0;
+      for (int sb = 0; sb < SUB; ++sb) v += sStage[(((sb * COMBOS + cb) * NLV + lam) * 32 + ln) * 4 + j];
+      const int t = (cb & 1) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb >> 1) * 8 + 2 * (ln & 3) + (j & 1);
+      sL[(lam * 32 + t) * NBP + c] = (double)v;
+    }
+    __syncthreads();
+    for (int o = tid; o < kp * nb; o += NT) {
+      const int t = o / nb, c = o - t * nb;
+      double s = sL[((NLV - 1) * 32 + t) * NBP + c];
+      for (int lam = NLV - 2; lam >= 0; --lam) s = fma(s, 0x1p-7, sL[(lam * 32 + t) * NBP + c]);
+      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14);
+    }
+    __syncthreads();
+    // D' = T^T D
+    for (int o = tid; o < kp * nb; o += NT) {
+      const int t = o % kp, cc = o / kp;
+      double e2 = 0.0;
+      for (int sidx = 0; sidx <= t; ++sidx) e2 = fma(cs.s_T[t * (t + 1) / 2 + sidx], cs.s_D[sidx * CB + cc], e2);
+      cs.s_E[t * CB + cc] = e2;
+    }
+    __syncthreads();
+    // digits of D' under a column scale: warp c, lane t
+    unsigned short* sE = sB;  // ND x NBP x SE
+    for (int c = warp; c < NBP; c += NW) {
+      const double v = (c < nb && lane < kp) ? cs.s_E[lane * CB + c] : 0.0;
+      const int ee = __reduce_max_sync(0xffffffffu, ebound(v));
+      unsigned ha, la;
+      halves28(fix56(v, 56 - ee), ha, la);
+      const unsigned hb = __shfl_down_sync(0xffffffffu, ha, 1), lb = __shfl_down_sync(0xffffffffu, la, 1);
+      const bool nega = v < 0.0;
+      const bool negb = __shfl_down_sync(0xffffffffu, nega ? 1 : 0, 1) != 0;
+      unsigned sg, nb2;
+      sign2(nega, negb, sg, nb2);
+      if ((lane & 1) == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sE + (k * NBP + c) * SE + lane) = dig2k(k, ha, la, hb, lb, sg, nb2);
+      }
+      if (lane == 0) s_Ee[c] = ee;
+    }
+    __syncthreads();
+    // ---- pass 2
+    const bool act2 = warp < 8 * NTN;
+    const int rt = warp & 7, nt2 = warp >> 3;
+    double nrm0 = 0.0, nrm1 = 0.0;
+    for (int rb = 0; rb < L; rb += R2) {
+      const int nr = min(R2, L - rb);
+      __syncthreads();
+      stage(rb, R2);
+      __syncthreads();
+      if (act2) {
+        float a2[NLV][4];
+#pragma unroll
+        for (int l = 0; l < NLV; ++l)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) a2[l][j] = 0.f;
+        const int r0 = rt * 16;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          unsigned eb[ND][2];
+#pragma unroll
+          for (int l = 0; l < ND; ++l)
+            ldsm_x2(eb[l], sE + (l * NBP + nt2 * 8 + (lane & 7)) * SE + ks * 16 + ((lane >> 3) & 1) * 8);
+#pragma unroll
+          for (int k = 0; k < ND; ++k) {
+            unsigned a[4];
+            ldsm_x4(a, sA + (k * RMAX + r0 + (lane & 7) + ((lane >> 3) & 1) * 8) * SA + ks * 16 + ((lane >> 4) & 1) * 8);
+#pragma unroll
+            for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(a2[k + l], a, eb[l]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int rr = r0 + g + ((j >> 1) << 3), c = nt2 * 8 + 2 * tq + (j & 1);
+          if (rr < nr && c < nb) {
+            long long u = 0;
+#pragma unroll
+            for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
+            u += (long long)(__float2int_rn(a2[7][j]) >> 6);
+            u += (long long)(__float2int_rn(a2[8][j]) >> 13);
+            double* p = commit_col(cs.s_cid, c) + rb + rr;
+            const double x = fma(-(double)u, pow2d(sEr[rr] + s_Ee[c] - 57), ldcg(p));
+            *p = x;
+            if (rb + rr >= kp) {
+              if (j & 1) nrm1 = fma(x, x, nrm1);
+              else nrm0 = fma(x, x, nrm0);
+            }
+          }
+        }
+      }
+    }
+    // trailing norms: lanes of one column quad, then the 8 row tiles in order
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      nrm0 += __shfl_xor_sync(0xffffffffu, nrm0, o);
+      nrm1 += __shfl_xor_sync(0xffffffffu, nrm1, o);
+    }
+    if (act2 && lane < 4) {
+      cs.s_nrm[rt * CB + nt2 * 8 + 2 * lane] = nrm0;
+      cs.s_nrm[rt * CB + nt2 * 8 + 2 * lane + 1] = nrm1;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      double v = 0.0;
+      for (int r8 = 0; r8 < 8; ++r8) v += cs.s_nrm[r8 * CB + tid];
+      if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
+    }
+  }
+
 
   // Commit for kp <= 4 (one-column LH steps and short J): V staged once for
   // all L rows, then one warp per column does D = V^T x (lanes over rows,
@@ -1809,11 +2090,20 @@ struct Engine {
       return sync();
     }
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
+    // the tensor-core form needs this panel's reflector digits
+    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 65536;
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
       __syncthreads();
       if (tid < nb) s_cid[tid] = s_list[base + tid];
       __syncthreads();
+      if constexpr (std::is_same<Team, GridTeam>::value) {  // only whole-grid teams have digits
+        if (tc) {
+          if (nb <= 8) commit_tc<8>(cs, nb);
+          else commit_tc<16>(cs, nb);
+          continue;
+        }
+      }
       switch (nb) {
         case 1: commit_batch<1>(cs); break;
         case 2: commit_batch<2>(cs); break;
