@@ -1698,65 +1698,125 @@ struct Engine {
   }
 
   // One batch of nb <= NBP (8 or 16) columns through the bf16 tensor cores,
-  // for 5 <= kp <= 32 with the panel's reflector digits in Vd/Ver.
+  // for 5 <= kp <= 16 KT (KT = 1 or 2 tiles of 16 reflectors) with the
+  // panel's reflector digits in Vd/Ver.
   //  pass 1: D = V^T C.  With V(r, :) = 2^Er v'(r, :) (|v'| < 1, digits a_k
   //    from the panel) and C' = 2^Er C (digits c_l under the column scale
-  //    2^Ec), D = 2^(Ec-14) sum_lam 2^(-7 lam) sum_{k+l=lam} a_k^T c_l.  Warp
-  //    (combo, sub) takes rows sub*16 .. +15 of every chunk for one 16 x 8
-  //    (reflector, column) tile and keeps one FP32 accumulator per level
-  //    k + l, moved to int32 every 128 of its rows (exact: at most 8 pairs of
-  //    products below 2^14 per row).
+  //    2^Ec), D = 2^(Ec-14) sum_lam 2^(-7 lam) sum_{k+l=lam} a_k^T c_l.
+  //    64-row chunks, double-buffered: the next chunk's V digits arrive by
+  //    cp.async and its C values are loaded while the tensor cores work on
+  //    the current one.  Warp (tile pair, sub) takes rows sub*16 .. +15 of
+  //    every chunk for one 16 x 8 (reflector, column) tile and keeps one
+  //    FP32 accumulator per level k + l <= 8, moved to int32 every 128 of
+  //    its rows (exact: at most 8 pairs of products below 2^14 per row).
   //  D' = T^T D in FP64.
-  //  pass 2: C -= V D'.  From the digits of V (row scale) and of D' (column
-  //    scale 2^Ee) warp (row tile, column tile) forms the 9 level sums of its
-  //    16 x 8 tile (exact in FP32: at most 8 pairs x 32 terms), combines them
-  //    in int64 (u = sum_lam lev_lam 2^(43-7 lam), levels 7 and 8 rounded
-  //    down; |u| < 2^63 as lev_lam < (lam+1) 2^19) and applies
-  //    x -= u 2^(Er+Ee-57) and the trailing norm in FP64.
+  //  pass 2: C -= V D'.  128-row chunks, double-buffered.  From the digits
+  //    of V (row scale) and of D' (column scale 2^Ee) warp (row tile, column
+  //    tile) forms the 9 level sums of its 16 x 8 tile (exact in FP32: at
+  //    most 8 pairs x 32 terms), combines them in int64
+  //    (u = sum_lam lev_lam 2^(43-7 lam), levels 7 and 8 rounded down;
+  //    |u| < 2^63 as lev_lam < (lam+1) 2^19) and applies x -= u 2^(Er+Ee-57)
+  //    and the trailing norm in FP64.
   // Every sum is exact or in a fixed order, so the result is bitwise
-  // reproducible.
-  template <int NBP>
+  // reproducible.  Shared memory (bytes of the work area): V digit buffers
+  // [0, 64K) and [64K, 128K) (ND planes of R rows x 64 B, 16-byte chunks
+  // XOR-swizzled by row so that ldmatrix is conflict-free), pass-1 C' digit
+  // buffers in the upper halves of those (pass 1 has R = 64), D' digits at
+  // 128K.
+  template <int NBP, int KT>
   __device__ void commit_tc(const CommitShape& cs, int nb) {
     constexpr int NTN = NBP / 8;           // column tiles
-    constexpr int COMBOS = 2 * NTN;        // (reflector tile, column tile) pairs
-    constexpr int SUB = NW / COMBOS;       // pass-1 warps per pair
-    constexpr int R1 = 16 * SUB;           // pass-1 rows per chunk (64 or 128)
-    constexpr int R2 = 128;                // pass-2 rows per chunk
-    constexpr int RMAX = 128;
-    constexpr int SA = 40;                 // row stride of staged V digits (bf16)
+    constexpr int COMBOS = KT * NTN;       // (reflector tile, column tile) pairs
+    constexpr int MW = COMBOS * 4;         // pass-1 MMA warps
+    constexpr int R1 = 64, R2 = 128;       // rows per chunk in pass 1 and 2
+    constexpr int BUF = ND * 128 * 32;     // bf16 per V digit buffer
     constexpr int SB = R1 + 8;             // row stride of C' digits (bf16)
     constexpr int SE = 40;                 // row stride of D' digits (bf16)
     const int L = cs.L;
-    unsigned short* sA = reinterpret_cast<unsigned short*>(cs.wk);  // ND x RMAX x SA
-    unsigned short* sB = sA + ND * RMAX * SA;                         // ND x NBP x SB
-    int* sEr = reinterpret_cast<int*>(sB + ND * NBP * SB);           // RMAX row exponents
+    unsigned short* sV = reinterpret_cast<unsigned short*>(cs.wk);
+    unsigned short* sE = sV + 2 * BUF;
     __shared__ int s_Ec[CB], s_Ee[CB];
     const int g = lane >> 2, tq = lane & 3;
-    // V digits of rows rb .. rb+R (zero past L) and their row exponents
-    auto stage = [&](int rb, int R) {
-      const int nr = min(R, L - rb);
+    // digit plane k of a chunk of R rows: R x 32 bf16, 16-byte chunk q of
+    // row r at chunk q ^ ((r >> 1) & 3)
+    auto vaddr = [&](const unsigned short* base, int R, int k, int r, int q) {
+      return base + (k * R + r) * 32 + ((q ^ ((r >> 1) & 3)) << 3);
+    };
+    // V digits of rows rb .. rb+R (zero past L) into buffer b
+    auto stage_v = [&](int rb, int R, int b) {
+      unsigned short* dst = sV + b * BUF;
       for (int e = tid; e < ND * R * 4; e += NT) {
         const int k = e / (R * 4), rem = e - k * (R * 4), rr = rem >> 2, q = rem & 3;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (rr < nr) v = __ldcg(reinterpret_cast<const uint4*>(I.Vd + ((size_t)k * I.m + rb + rr) * 16) + q);
-        *reinterpret_cast<uint4*>(sA + (k * RMAX + rr) * SA + q * 8) = v;
+        const bool ok = rb + rr < L;
+        cp16(dst + (k * R + rr) * 32 + ((q ^ ((rr >> 1) & 3)) << 3), I.Vd + ((size_t)k * I.m + (ok ? rb + rr : 0)) * 16 + q * 4, ok);
       }
-      if (tid < R) sEr[tid] = (tid < nr) ? ldcg(I.Ver + rb + tid) : 0;
+      cp_commit();
     };
-    // column scales of C' = 2^Er C
-    for (int c = warp; c < nb; c += NW) {
+    // column scales of C' = 2^Er C: (column, row quarter) per warp, 8 rows
+    // per lane in flight
+    if (tid < CB) s_Ec[tid] = -8000;
+    __syncthreads();
+    for (int p = warp; p < nb * 4; p += NW) {
+      const int c = p >> 2;
       const double* col = commit_col(cs.s_cid, c);
+      int lo, hi;
+      split(L, 4, p & 3, lo, hi);
       int mx = -8000;
-      for (int r = lane; r < L; r += 32) {
-        const int e = ebound(ldcg(col + r));
-        if (e > -2000) mx = max(mx, e + ldcg(I.Ver + r));
+      for (int r0 = lo + lane; r0 < hi; r0 += 256) {
+        double xv[8];
+        int ev[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = r0 + 32 * u;
+          xv[u] = (r < hi) ? ldcg(col + r) : 0.0;
+          ev[u] = (r < hi) ? ldcg(I.Ver + r) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = ebound(xv[u]);
+          if (e > -2000) mx = max(mx, e + ev[u]);
+        }
       }
       mx = __reduce_max_sync(0xffffffffu, mx);
-      if (lane == 0) s_Ec[c] = mx;
+      if (lane == 0) atomicMax(&s_Ec[c], mx);
     }
+    __syncthreads();
     // ---- pass 1
+    const int nch1 = (L + R1 - 1) / R1;
+    const bool mw = warp < MW;
     const int cmb = warp % COMBOS, sub = warp / COMBOS;
-    const int mt = cmb & 1, nt = cmb >> 1;
+    const int mt = cmb % KT, nt = cmb / KT;
+    // C' digits: thread (column tid/32, row pair tid%32) of each chunk
+    const bool dw = tid < NBP * 32;
+    const int dc = tid >> 5, drr = 2 * (tid & 31);
+    const double* dcol = (dw && dc < nb) ? commit_col(cs.s_cid, dc) : nullptr;
+    const int dec = (dw && dc < nb) ? s_Ec[dc] : 0;
+    double xa = 0.0, xb = 0.0;
+    int era = 0, erb = 0;
+    auto fetch_c = [&](int rb) {
+      xa = xb = 0.0;
+      era = erb = 0;
+      if (dcol) {
+        if (rb + drr < L) {
+          xa = ldcg(dcol + rb + drr);
+          era = ldcg(I.Ver + rb + drr);
+        }
+        if (rb + drr + 1 < L) {
+          xb = ldcg(dcol + rb + drr + 1);
+          erb = ldcg(I.Ver + rb + drr + 1);
+        }
+      }
+    };
+    auto digits_c = [&](int b) {
+      if (!dw) return;
+      unsigned short* sBb = sV + b * BUF + BUF / 2;
+      unsigned ha, la, hb, lb, sg, nb2;
+      halves28(fix56(xa, era + 56 - dec), ha, la);
+      halves28(fix56(xb, erb + 56 - dec), hb, lb);
+      sign2(xa < 0.0, xb < 0.0, sg, nb2);
+#pragma unroll
+      for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sBb + (k * NBP + dc) * SB + drr) = dig2k(k, ha, la, hb, lb, sg, nb2);
+    };
     float acc[NLV][4];
     int iacc[NLV][4];
 #pragma unroll
@@ -1767,49 +1827,36 @@ struct Engine {
         iacc[l][j] = 0;
       }
     int since = 0;
-    for (int rb = 0; rb < L; rb += R1) {
-      const int nr = min(R1, L - rb);
+    stage_v(0, R1, 0);
+    fetch_c(0);
+    digits_c(0);
+    for (int jc = 0; jc < nch1; ++jc) {
+      const int rb = jc * R1, b = jc & 1;
+      cp_wait_all();
       __syncthreads();
-      stage(rb, R1);
-      __syncthreads();
-      // digits of C': thread (column, row pair), one bf16 pair per digit
-      for (int e = tid; e < NBP * (R1 / 2); e += NT) {
-        const int c = e / (R1 / 2), rr = 2 * (e - c * (R1 / 2));
-        unsigned w[ND];
-        if (c < nb) {
-          const double* col = commit_col(cs.s_cid, c) + rb;
-          const double xa = (rr < nr) ? ldcg(col + rr) : 0.0;
-          const double xb = (rr + 1 < nr) ? ldcg(col + rr + 1) : 0.0;
-          const int ec = s_Ec[c];
-          unsigned ha, la, hb, lb, sg, nb2;
-          halves28(fix56(xa, sEr[rr] + 56 - ec), ha, la);
-          halves28(fix56(xb, sEr[rr + 1] + 56 - ec), hb, lb);
-          sign2(xa < 0.0, xb < 0.0, sg, nb2);
-#pragma unroll
-          for (int k = 0; k < ND; ++k) w[k] = dig2k(k, ha, la, hb, lb, sg, nb2);
-        } else {
-#pragma unroll
-          for (int k = 0; k < ND; ++k) w[k] = 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sB + (k * NBP + c) * SB + rr) = w[k];
+      if (jc + 1 < nch1) {
+        stage_v(rb + R1, R1, b ^ 1);
+        fetch_c(rb + R1);
       }
-      __syncthreads();
-      {
+      if (mw) {
+        const unsigned short* sAb = sV + b * BUF;
+        const unsigned short* sBb = sAb + BUF / 2;
         const int r0 = sub * 16;
         unsigned bq[ND][2];
 #pragma unroll
-        for (int l = 0; l < ND; ++l) ldsm_x2(bq[l], sB + (l * NBP + nt * 8 + (lane & 7)) * SB + r0 + ((lane >> 3) & 1) * 8);
+        for (int l = 0; l < ND; ++l) ldsm_x2(bq[l], sBb + (l * NBP + nt * 8 + (lane & 7)) * SB + r0 + ((lane >> 3) & 1) * 8);
+        const int ra = r0 + (lane & 7) + ((lane >> 4) << 3), qa = mt * 2 + ((lane >> 3) & 1);
 #pragma unroll
         for (int k = 0; k < ND; ++k) {
           unsigned a[4];
-          ldsm_x4_t(a, sA + (k * RMAX + r0 + (lane & 7) + ((lane >> 4) << 3)) * SA + mt * 16 + ((lane >> 3) & 1) * 8);
+          ldsm_x4_t(a, vaddr(sAb, R1, k, ra, qa));
 #pragma unroll
           for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(acc[k + l], a, bq[l]);
         }
       }
+      if (jc + 1 < nch1) digits_c(b ^ 1);
       since += 16;
-      if (since == 128 || rb + R1 >= L) {
+      if (since == 128 || jc + 1 == nch1) {
 #pragma unroll
         for (int l = 0; l < NLV; ++l)
 #pragma unroll
@@ -1822,18 +1869,20 @@ struct Engine {
     }
     // sum over the sub-blocks (exact, int64) and D from the level sums
     __syncthreads();
-    int* sStage = reinterpret_cast<int*>(sA);                             // NW x NLV x 32 x 4 (72 KB)
-    double* sL = reinterpret_cast<double*>(reinterpret_cast<char*>(sA) + 73728);  // NLV x 32 x NBP
+    int* sStage = reinterpret_cast<int*>(sV);                                     // MW x NLV x 32 x 4
+    double* sL = reinterpret_cast<double*>(reinterpret_cast<char*>(sV) + 73728);  // NLV x 32 x NBP
+    if (mw) {
 #pragma unroll
-    for (int l = 0; l < NLV; ++l)
+      for (int l = 0; l < NLV; ++l)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) sStage[((warp * NLV + l) * 32 + lane) * 4 + j] = iacc[l][j];
+        for (int j = 0; j < 4; ++j) sStage[((warp * NLV + l) * 32 + lane) * 4 + j] = iacc[l][j];
+    }
     __syncthreads();
     for (int e = tid; e < COMBOS * NLV * 128; e += NT) {
       const int j = e & 3, ln = (e >> 2) & 31, lam = (e >> 7) % NLV, cb = (e >> 7) / NLV;
       long long v = 0;
-      for (int sb = 0; sb < SUB; ++sb) v += sStage[(((sb * COMBOS + cb) * NLV + lam) * 32 + ln) * 4 + j];
-      const int t = (cb & 1) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb >> 1) * 8 + 2 * (ln & 3) + (j & 1);
+      for (int sb = 0; sb < 4; ++sb) v += sStage[(((sb * COMBOS + cb) * NLV + lam) * 32 + ln) * 4 + j];
+      const int t = (cb % KT) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb / KT) * 8 + 2 * (ln & 3) + (j & 1);
       sL[(lam * 32 + t) * NBP + c] = (double)v;
     }
     __syncthreads();
@@ -1853,7 +1902,6 @@ struct Engine {
     }
     __syncthreads();
     // digits of D' under a column scale: warp c, lane t
-    unsigned short* sE = sB;  // ND x NBP x SE
     for (int c = warp; c < NBP; c += NW) {
       const double v = (c < nb && lane < kp) ? cs.s_E[lane * CB + c] : 0.0;
       const int ee = __reduce_max_sync(0xffffffffu, ebound(v));
@@ -1872,23 +1920,38 @@ struct Engine {
     }
     __syncthreads();
     // ---- pass 2
+    const int nch2 = (L + R2 - 1) / R2;
     const bool act2 = warp < 8 * NTN;
     const int rt = warp & 7, nt2 = warp >> 3;
+    const int c0 = nt2 * 8 + 2 * tq;
+    double* colp0 = (act2 && c0 < nb) ? commit_col(cs.s_cid, c0) : nullptr;
+    double* colp1 = (act2 && c0 + 1 < nb) ? commit_col(cs.s_cid, c0 + 1) : nullptr;
+    const int ee0 = s_Ee[c0], ee1 = s_Ee[c0 + 1];
     double nrm0 = 0.0, nrm1 = 0.0;
-    for (int rb = 0; rb < L; rb += R2) {
-      const int nr = min(R2, L - rb);
+    stage_v(0, R2, 0);
+    for (int jc = 0; jc < nch2; ++jc) {
+      const int rb = jc * R2, b = jc & 1;
+      cp_wait_all();
       __syncthreads();
-      stage(rb, R2);
-      __syncthreads();
+      if (jc + 1 < nch2) stage_v(rb + R2, R2, b ^ 1);
       if (act2) {
+        // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
+        const int ra = rb + rt * 16 + g, rb8 = ra + 8;
+        double xv[4];
+        xv[0] = (colp0 && ra < L) ? ldcg(colp0 + ra) : 0.0;
+        xv[1] = (colp1 && ra < L) ? ldcg(colp1 + ra) : 0.0;
+        xv[2] = (colp0 && rb8 < L) ? ldcg(colp0 + rb8) : 0.0;
+        xv[3] = (colp1 && rb8 < L) ? ldcg(colp1 + rb8) : 0.0;
+        const int er0 = (ra < L) ? ldcg(I.Ver + ra) : 0, er1 = (rb8 < L) ? ldcg(I.Ver + rb8) : 0;
         float a2[NLV][4];
 #pragma unroll
         for (int l = 0; l < NLV; ++l)
 #pragma unroll
           for (int j = 0; j < 4; ++j) a2[l][j] = 0.f;
-        const int r0 = rt * 16;
+        const unsigned short* sAb = sV + b * BUF;
+        const int r0 = rt * 16, rq = r0 + (lane & 7) + ((lane >> 3) & 1) * 8;
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
+        for (int ks = 0; ks < KT; ++ks) {
           unsigned eb[ND][2];
 #pragma unroll
           for (int l = 0; l < ND; ++l)
@@ -1896,24 +1959,24 @@ struct Engine {
 #pragma unroll
           for (int k = 0; k < ND; ++k) {
             unsigned a[4];
-            ldsm_x4(a, sA + (k * RMAX + r0 + (lane & 7) + ((lane >> 3) & 1) * 8) * SA + ks * 16 + ((lane >> 4) & 1) * 8);
+            ldsm_x4(a, vaddr(sAb, R2, k, rq, ks * 2 + ((lane >> 4) & 1)));
 #pragma unroll
             for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(a2[k + l], a, eb[l]);
           }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int rr = r0 + g + ((j >> 1) << 3), c = nt2 * 8 + 2 * tq + (j & 1);
-          if (rr < nr && c < nb) {
+          const int row = (j < 2) ? ra : rb8;
+          double* p = (j & 1) ? colp1 : colp0;
+          if (p && row < L) {
             long long u = 0;
 #pragma unroll
             for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
-            double* p = commit_col(cs.s_cid, c) + rb + rr;
-            const double x = fma(-(double)u, pow2d(sEr[rr] + s_Ee[c] - 57), ldcg(p));
-            *p = x;
-            if (rb + rr >= kp) {
+            const double x = fma(-(double)u, pow2d(((j < 2) ? er0 : er1) + ((j & 1) ? ee1 : ee0) - 57), xv[j]);
+            p[row] = x;
+            if (row >= kp) {
               if (j & 1) nrm1 = fma(x, x, nrm1);
               else nrm0 = fma(x, x, nrm0);
             }
@@ -2099,8 +2162,13 @@ struct Engine {
       __syncthreads();
       if constexpr (std::is_same<Team, GridTeam>::value) {  // only whole-grid teams have digits
         if (tc) {
-          if (nb <= 8) commit_tc<8>(cs, nb);
-          else commit_tc<16>(cs, nb);
+          if (kp <= 16) {
+            if (nb <= 8) commit_tc<8, 1>(cs, nb);
+            else commit_tc<16, 1>(cs, nb);
+          } else {
+            if (nb <= 8) commit_tc<8, 2>(cs, nb);
+            else commit_tc<16, 2>(cs, nb);
+          }
           continue;
         }
       }
