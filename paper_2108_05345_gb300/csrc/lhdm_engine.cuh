@@ -115,7 +115,7 @@ struct Inst {
 };
 
 // control words (ctl[])
-enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR };
+enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK };
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -292,6 +292,16 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, bool ok) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 16 : 0)
                : "memory");
 }
+// 8- and 4-byte asynchronous copies global -> shared (zero fill when !ok)
+__device__ __forceinline__ void cp8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // 2^e as a double (normal range) or via ldexp
@@ -306,9 +316,12 @@ __device__ __forceinline__ double pow2d(int e) {
 // *err on expiry, after which every CTA leaves the solve.
 struct GridTeam {
   int rank, size;
-  unsigned int* bar;  // [0] arrivals, [1] generation
+  unsigned int* bar;  // [0] arrivals, [1] generation; [2], [3] the same for sub-teams
   int* err;
-  __device__ __forceinline__ bool sync() {
+  __device__ __forceinline__ bool sync() { return sync_words(bar, size); }
+  // barrier of ranks 0 .. n-1 only (the other ranks must not call it)
+  __device__ __forceinline__ bool sync_sub(int n) { return sync_words(bar + 2, n); }
+  __device__ __forceinline__ bool sync_words(unsigned int* bw, int n) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -316,14 +329,14 @@ struct GridTeam {
       // which is cumulative: one fence per CTA publishes them
       __threadfence();
       int ok = 1;
-      volatile unsigned int* gen = bar + 1;
+      volatile unsigned int* gen = bw + 1;
       const unsigned int g = *gen;
       __threadfence();
-      const unsigned int prev = atomicAdd(bar, 1u);
-      if (prev == (unsigned int)size - 1u) {
-        atomicExch(bar, 0u);
+      const unsigned int prev = atomicAdd(bw, 1u);
+      if (prev == (unsigned int)n - 1u) {
+        atomicExch(bw, 0u);
         __threadfence();
-        atomicAdd(bar + 1, 1u);
+        atomicAdd(bw + 1, 1u);
       } else {
         const long long t0 = gtimer();
         unsigned int spins = 0;
@@ -351,6 +364,7 @@ struct CtaTeam {
     __syncthreads();
     return true;
   }
+  __device__ __forceinline__ bool sync_sub(int) { return sync(); }
 };
 
 // Bounded wait until *flag >= target (one thread); false on timeout.

@@ -605,15 +605,26 @@ struct Engine {
   // a reflector are formed once per CTA and shared; T is built by rank 0
   // after the last reflector from the saved products z_s = v_s^T v_i.
   // (FP64 issue is the scarce resource here: every warp instruction counts.)
-  static constexpr int PR_MAX = 64;
+  static constexpr int PR_MAX = 128;     // rows per CTA of the shared-memory panel
+  static constexpr int PANEL_ROWS = 32;  // target rows per panel CTA
   static constexpr int PS = KM + 1;  // row stride of the staged panel
   static constexpr int RED_U = 12;   // partial-sum loads in flight per thread
-  __device__ bool panel_smem(const int* s_J) {
+  __device__ bool panel_smem(const int* s_J, int P) {
     const int L = I.m - nP;
     if (kk > L) kk = L;
+    if (tm.rank < P && !panel_rows(s_J, P, L)) return false;
+    if (tm.rank == 0 && tid == 0) I.ctl[C_KK] = kk;
+    if (!sync()) return false;
+    kk = ldcg(I.ctl + C_KK);
+    vd_ok = I.Vd != nullptr && kk > 4 && kk <= 32;
+    return true;
+  }
+  // The panel on ranks 0 .. P-1 (rows split over them), with the sub-team
+  // barrier; kk is left at the number of reflectors formed.
+  __device__ bool panel_rows(const int* s_J, int P, int L) {
     const int k0 = kk, NL = k0 + 1;
     int q0, q1;
-    split(L, tm.size, tm.rank, q0, q1);
+    split(L, P, tm.rank, q0, q1);
     const int nr = q1 - q0;
     double* sP = dyn;                   // nr x PS: own rows, columns 0..k0 (k0 = Q^T b)
     double* sZ = dyn + PR_MAX * PS;     // KM x KM, rank 0: z_s of reflector i at sZ[s + i KM]
@@ -632,15 +643,19 @@ struct Engine {
     __syncthreads();
     // owner of a panel row: the rank whose split range holds it
     auto owner = [&](int row) {
-      int r = (int)(((long long)row * tm.size) / max(L, 1));
+      int r = (int)(((long long)row * P) / max(L, 1));
       int lo, hi;
       for (;;) {
-        split(L, tm.size, r, lo, hi);
+        split(L, P, r, lo, hi);
         if (row < lo) --r;
         else if (row >= hi) ++r;
         else return r;
       }
     };
+    // owners of the pivot rows 0 .. k0-1 (k0 <= L), once per panel
+    __shared__ int s_own[KM];
+    if (tid < k0) s_own[tid] = owner(tid);
+    __syncthreads();
     // thread (gl, gg): column gl, group gg of G
     const int G = NT / NL, gl = tid % NL, gg = tid / NL;
     const bool actg = gg < G;
@@ -687,16 +702,16 @@ struct Engine {
       }
       if (i >= q0 && i < q1 && tid <= k0) mypart[pb + 2 * (KM + 1) + tid] = sP[(i - q0) * PS + tid];
       if (i + 1 >= q0 && i + 1 < q1 && tid <= k0) mypart[pb + 3 * (KM + 1) + tid] = sP[(i + 1 - q0) * PS + tid];
-      if (!sync()) return false;
+      if (!tm.sync_sub(P)) return false;
       {
-        const int own = owner(i), own2 = owner(i + 1);
+        const int own = s_own[i], own2 = s_own[i + 1];
         if (tid <= k0) {
           s_piv[tid] = ldcg(I.part + (size_t)own * PW + pb + 2 * (KM + 1) + tid);
           s_piv2[tid] = ldcg(I.part + (size_t)own2 * PW + pb + 3 * (KM + 1) + tid);
         }
         if (actg) {
           // ranks gg, gg + G, ...: every load of a round in flight at once
-          const int cnt = (tm.size - gg + G - 1) / G;
+          const int cnt = (P - gg + G - 1) / G;
           double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
           for (int j0 = 0; j0 < cnt; j0 += RED_U) {
             double v[RED_U], w[RED_U];
@@ -868,15 +883,15 @@ struct Engine {
         if (tid <= k0) mypart[pb + tid] = sG[tid];
       }
       if (i >= q0 && i < q1 && tid <= k0) mypart[2 * (KM + 1) + pb + tid] = sP[(i - q0) * PS + tid];
-      if (!sync()) return false;
+      if (!tm.sync_sub(P)) return false;
       // every CTA reduces the team's dots: thread (gl, gg) adds ranks gg,
       // gg + G, ... (loads first), then a pairwise tree over gg; the pivot
       // row comes from its owner
       {
-        const int own = owner(i);
+        const int own = s_own[i];
         if (tid <= k0) s_piv[tid] = ldcg(I.part + (size_t)own * PW + 2 * (KM + 1) + pb + tid);
         if (actg) {
-          const int cnt = (tm.size - gg + G - 1) / G;
+          const int cnt = (P - gg + G - 1) / G;
           double a0 = 0.0, a1 = 0.0;
           for (int j0 = 0; j0 < cnt; j0 += RED_U) {
             double v[RED_U];
@@ -952,8 +967,7 @@ struct Engine {
     // the same rows as 7-bit digits for the tensor-core commit: one warp per
     // row, lane t holds V(row, t) (v0 on the diagonal, zero above), the row
     // scale is its largest exponent bound, and even lanes store digit pairs
-    vd_ok = I.Vd != nullptr && kk > 4 && kk <= 32;
-    if (vd_ok) {
+    if (I.Vd != nullptr && kk > 4 && kk <= 32) {
       for (int rr = warp; rr < nr; rr += NW) {
         const int row = q0 + rr;
         const double v = (lane < kk) ? (row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0)) : 0.0;
@@ -997,7 +1011,7 @@ struct Engine {
         if (r <= c) I.T[r + c * KM] = sT[r + c * KM];
       }
     }
-    return sync();
+    return true;
   }
 
   // Back substitution with the kk x kk triangle R22 (one warp).
@@ -1786,33 +1800,33 @@ struct Engine {
     const bool mw = warp < MW;
     const int cmb = warp % COMBOS, sub = warp / COMBOS;
     const int mt = cmb % KT, nt = cmb / KT;
-    // C' digits: thread (column tid/32, row pair tid%32) of each chunk
+    // C' digits: thread (column tid/32, row pair tid%32) of each chunk, from
+    // the chunk's C values and row exponents, staged by cp.async in the
+    // buffer's [50K, 58.25K) bytes
     const bool dw = tid < NBP * 32;
     const int dc = tid >> 5, drr = 2 * (tid & 31);
-    const double* dcol = (dw && dc < nb) ? commit_col(cs.s_cid, dc) : nullptr;
     const int dec = (dw && dc < nb) ? s_Ec[dc] : 0;
-    double xa = 0.0, xb = 0.0;
-    int era = 0, erb = 0;
-    auto fetch_c = [&](int rb) {
-      xa = xb = 0.0;
-      era = erb = 0;
-      if (dcol) {
-        if (rb + drr < L) {
-          xa = ldcg(dcol + rb + drr);
-          era = ldcg(I.Ver + rb + drr);
-        }
-        if (rb + drr + 1 < L) {
-          xb = ldcg(dcol + rb + drr + 1);
-          erb = ldcg(I.Ver + rb + drr + 1);
-        }
+    auto cstage = [&](int b) { return reinterpret_cast<double*>(sV + b * BUF) + 6400; };
+    auto stage_c = [&](int rb, int b) {
+      double* sC = cstage(b);
+      int* sR = reinterpret_cast<int*>(sC + NBP * R1);
+      for (int e = tid; e < NBP * R1; e += NT) {
+        const int c = e / R1, r = e - c * R1;
+        const bool ok = c < nb && rb + r < L;
+        cp8(sC + e, ok ? commit_col(cs.s_cid, c) + rb + r : I.u, ok);
       }
+      if (tid < R1) cp4(sR + tid, rb + tid < L ? I.Ver + rb + tid : I.Ver, rb + tid < L);
+      cp_commit();
     };
     auto digits_c = [&](int b) {
       if (!dw) return;
+      const double* sC = cstage(b);
+      const int* sR = reinterpret_cast<const int*>(sC + NBP * R1);
+      const double xa = sC[dc * R1 + drr], xb = sC[dc * R1 + drr + 1];
       unsigned short* sBb = sV + b * BUF + BUF / 2;
       unsigned ha, la, hb, lb, sg, nb2;
-      halves28(fix56(xa, era + 56 - dec), ha, la);
-      halves28(fix56(xb, erb + 56 - dec), hb, lb);
+      halves28(fix56(xa, sR[drr] + 56 - dec), ha, la);
+      halves28(fix56(xb, sR[drr + 1] + 56 - dec), hb, lb);
       sign2(xa < 0.0, xb < 0.0, sg, nb2);
 #pragma unroll
       for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sBb + (k * NBP + dc) * SB + drr) = dig2k(k, ha, la, hb, lb, sg, nb2);
@@ -1827,16 +1841,23 @@ struct Engine {
         iacc[l][j] = 0;
       }
     int since = 0;
-    stage_v(0, R1, 0);
-    fetch_c(0);
+    // every CTA walks the chunks from its own starting chunk, so that the
+    // CTAs do not all ask for the same digit rows at the same moment (the
+    // sums are exact, so the order does not matter)
+    const int s1 = tm.rank % nch1;
+    auto row1 = [&](int jc) { return ((jc + s1) % nch1) * R1; };
+    stage_c(row1(0), 0);
+    stage_v(row1(0), R1, 0);
+    cp_wait_all();
+    __syncthreads();
     digits_c(0);
     for (int jc = 0; jc < nch1; ++jc) {
-      const int rb = jc * R1, b = jc & 1;
+      const int b = jc & 1;
       cp_wait_all();
       __syncthreads();
       if (jc + 1 < nch1) {
-        stage_v(rb + R1, R1, b ^ 1);
-        fetch_c(rb + R1);
+        stage_c(row1(jc + 1), b ^ 1);
+        stage_v(row1(jc + 1), R1, b ^ 1);
       }
       if (mw) {
         const unsigned short* sAb = sV + b * BUF;
@@ -1854,7 +1875,11 @@ struct Engine {
           for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(acc[k + l], a, bq[l]);
         }
       }
-      if (jc + 1 < nch1) digits_c(b ^ 1);
+      if (jc + 1 < nch1) {
+        cp_wait_prev();  // the next chunk's C values (its V digits may still be in flight)
+        __syncthreads();
+        digits_c(b ^ 1);
+      }
       since += 16;
       if (since == 128 || jc + 1 == nch1) {
 #pragma unroll
@@ -1928,12 +1953,14 @@ struct Engine {
     double* colp1 = (act2 && c0 + 1 < nb) ? commit_col(cs.s_cid, c0 + 1) : nullptr;
     const int ee0 = s_Ee[c0], ee1 = s_Ee[c0 + 1];
     double nrm0 = 0.0, nrm1 = 0.0;
-    stage_v(0, R2, 0);
+    const int s2 = tm.rank % nch2;
+    auto row2 = [&](int jc) { return ((jc + s2) % nch2) * R2; };
+    stage_v(row2(0), R2, 0);
     for (int jc = 0; jc < nch2; ++jc) {
-      const int rb = jc * R2, b = jc & 1;
+      const int rb = row2(jc), b = jc & 1;
       cp_wait_all();
       __syncthreads();
-      if (jc + 1 < nch2) stage_v(rb + R2, R2, b ^ 1);
+      if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
         // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
         const int ra = rb + rt * 16 + g, rb8 = ra + 8;
@@ -2920,9 +2947,12 @@ struct Engine {
       kdm = kk;
       phase(PH_PANEL);
       {
+        // the shared-memory panel runs on about Lp / PANEL_ROWS CTAs: its
+        // exchanges then move far fewer partial sums
         const int Lp = I.m - nP;
-        const bool in_smem = (Lp + tm.size - 1) / tm.size <= PR_MAX && tm.size <= 24 * (NT / (KM + 1));
-        if (!(in_smem ? panel_smem(s_J) : panel(s_J))) return fail_out();
+        const int P = min(tm.size, max(1, (Lp + PANEL_ROWS - 1) / PANEL_ROWS));
+        const bool in_smem = (Lp + P - 1) / P <= PR_MAX;
+        if (!(in_smem ? panel_smem(s_J, P) : panel(s_J))) return fail_out();
       }
       if (kk == 0) {
         rank_limited = 1;
