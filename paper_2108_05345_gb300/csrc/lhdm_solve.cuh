@@ -980,8 +980,11 @@ struct Engine {
         unsigned sg, nb2;
         sign2(nega, negb, sg, nb2);
         if ((lane & 1) == 0) {
+          // word lane/2 of the row; its 16-byte chunk is stored XOR-swizzled
+          // by row, as the commit's shared-memory digit planes expect
+          const int w = lane >> 1, wp = ((((w >> 2) ^ (row >> 1)) & 3) << 2) | (w & 3);
 #pragma unroll
-          for (int k = 0; k < ND; ++k) I.Vd[((size_t)k * I.m + row) * 16 + (lane >> 1)] = dig2k(k, ha, la, hb, lb, sg, nb2);
+          for (int k = 0; k < ND; ++k) I.Vd[((size_t)k * I.m + row) * 16 + wp] = dig2k(k, ha, la, hb, lb, sg, nb2);
         }
         if (lane == 0) I.Ver[row] = er;
       }
@@ -1738,7 +1741,7 @@ struct Engine {
   // buffers in the upper halves of those (pass 1 has R = 64), D' digits at
   // 128K.
   template <int NBP, int KT>
-  __device__ void commit_tc(const CommitShape& cs, int nb) {
+  __device__ bool commit_tc(const CommitShape& cs, int nb) {
     constexpr int NTN = NBP / 8;           // column tiles
     constexpr int COMBOS = KT * NTN;       // (reflector tile, column tile) pairs
     constexpr int MW = COMBOS * 4;         // pass-1 MMA warps
@@ -1756,15 +1759,50 @@ struct Engine {
     auto vaddr = [&](const unsigned short* base, int R, int k, int r, int q) {
       return base + (k * R + r) * 32 + ((q ^ ((r >> 1) & 3)) << 3);
     };
-    // V digits of rows rb .. rb+R (zero past L) into buffer b
+    // V digits of rows rb .. rb+R into buffer b: one bulk copy per digit
+    // plane (the rows are stored pre-swizzled), completing on the buffer's
+    // mbarrier; rows past L are zeroed by the threads.  Every thread orders
+    // its earlier generic writes of the work area before the async copies.
+    __shared__ unsigned long long s_mbar[2];
+    unsigned vph = 0u;  // bit b: parity of buffer b's next phase
+    fence_proxy_async();
+    if (tid == 0) {
+      mbar_init(&s_mbar[0], 1);
+      mbar_init(&s_mbar[1], 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
     auto stage_v = [&](int rb, int R, int b) {
       unsigned short* dst = sV + b * BUF;
-      for (int e = tid; e < ND * R * 4; e += NT) {
-        const int k = e / (R * 4), rem = e - k * (R * 4), rr = rem >> 2, q = rem & 3;
-        const bool ok = rb + rr < L;
-        cp16(dst + (k * R + rr) * 32 + ((q ^ ((rr >> 1) & 3)) << 3), I.Vd + ((size_t)k * I.m + (ok ? rb + rr : 0)) * 16 + q * 4, ok);
+      const int nr = min(R, L - rb);
+      if (tid == 0) {
+        mbar_expect_tx(&s_mbar[b], (unsigned)(ND * nr * 64));
+        for (int k = 0; k < ND; ++k)
+          bulk_g2s(dst + k * R * 32, I.Vd + ((size_t)k * I.m + rb) * 16, (unsigned)(nr * 64), &s_mbar[b]);
       }
-      cp_commit();
+      const int zq = (R - nr) * 4;  // 16-byte chunks past L per plane
+      for (int e = tid; e < ND * zq; e += NT) {
+        const int k = e / zq, rem = e - k * zq;
+        *reinterpret_cast<uint4*>(dst + (k * R + nr) * 32 + rem * 8) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      fence_proxy_async();
+    };
+    // wait for buffer b's copies (bounded); false on expiry
+    auto wait_v = [&](int b) -> bool {
+      const unsigned par = (vph >> b) & 1u;
+      vph ^= 1u << b;
+      const long long t0 = gtimer();
+      unsigned spins = 0;
+      while (!mbar_try_wait(&s_mbar[b], par)) {
+        if ((++spins & 255u) == 0u && gtimer() - t0 > WAIT_NS) return false;
+      }
+      return true;
+    };
+    auto expired = [&]() {
+      if (tid == 0) {
+        int* er = tm_err();
+        if (er) atomicExch(er, 1);
+      }
     };
     // column scales of C' = 2^Er C: (column, row quarter) per warp, 8 rows
     // per lane in flight
@@ -1853,8 +1891,11 @@ struct Engine {
     digits_c(0);
     for (int jc = 0; jc < nch1; ++jc) {
       const int b = jc & 1;
-      cp_wait_all();
-      __syncthreads();
+      const bool okv = wait_v(b);
+      if (__syncthreads_or(!okv)) {
+        expired();
+        return false;
+      }
       if (jc + 1 < nch1) {
         stage_c(row1(jc + 1), b ^ 1);
         stage_v(row1(jc + 1), R1, b ^ 1);
@@ -1876,7 +1917,7 @@ struct Engine {
         }
       }
       if (jc + 1 < nch1) {
-        cp_wait_prev();  // the next chunk's C values (its V digits may still be in flight)
+        cp_wait_all();  // the next chunk's C values (its V digits may still be in flight)
         __syncthreads();
         digits_c(b ^ 1);
       }
@@ -1955,11 +1996,16 @@ struct Engine {
     double nrm0 = 0.0, nrm1 = 0.0;
     const int s2 = tm.rank % nch2;
     auto row2 = [&](int jc) { return ((jc + s2) % nch2) * R2; };
+    fence_proxy_async();  // pass-1 scratch writes before the async copies
+    __syncthreads();
     stage_v(row2(0), R2, 0);
     for (int jc = 0; jc < nch2; ++jc) {
       const int rb = row2(jc), b = jc & 1;
-      cp_wait_all();
-      __syncthreads();
+      const bool okv = wait_v(b);
+      if (__syncthreads_or(!okv)) {
+        expired();
+        return false;
+      }
       if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
         // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
@@ -2027,6 +2073,7 @@ struct Engine {
       for (int r8 = 0; r8 < 8; ++r8) v += cs.s_nrm[r8 * CB + tid];
       if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
     }
+    return true;
   }
 
 
@@ -2189,13 +2236,10 @@ struct Engine {
       __syncthreads();
       if constexpr (std::is_same<Team, GridTeam>::value) {  // only whole-grid teams have digits
         if (tc) {
-          if (kp <= 16) {
-            if (nb <= 8) commit_tc<8, 1>(cs, nb);
-            else commit_tc<16, 1>(cs, nb);
-          } else {
-            if (nb <= 8) commit_tc<8, 2>(cs, nb);
-            else commit_tc<16, 2>(cs, nb);
-          }
+          bool ok;
+          if (kp <= 16) ok = (nb <= 8) ? commit_tc<8, 1>(cs, nb) : commit_tc<16, 1>(cs, nb);
+          else ok = (nb <= 8) ? commit_tc<8, 2>(cs, nb) : commit_tc<16, 2>(cs, nb);
+          if (!ok) return false;
           continue;
         }
       }
