@@ -106,7 +106,8 @@ struct Inst {
   double* accb;   // ceil(cap/TB) x TB slab accumulations of the pipelined solve
   int* tflag;     // ceil(cap/TB) block flags, ceil(cap/TB) * TB/SLAB slab flags, ceil(cap/TB) * INV_PARTS inverse flags
   unsigned long long* amask;  // KM acceptance masks
-  unsigned* Vd;   // panel reflectors as 7-bit digits: ND x m rows x 16 words (bf16 pairs), null: none
+  unsigned* Vd;   // panel reflectors as 7-bit digits: m rows x ND planes x 16 words (bf16 pairs,
+                  // 16-byte chunk c of row r at c ^ (r & 7)), null: none
   int* Ver;       // m: row scale exponents of Vd (|V(r, :)| < 2^Ver[r])
   double* phase_ns;           // NPHASE (may be null)
   int* trace;                 // 6 ints per outer step (may be null)

@@ -82,7 +82,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.pipelined = team > 1;
   L.Dinv = take(L.pipelined ? nbk * TB * TB : 1);
   L.accb = take(L.pipelined ? nbk * TB : 1);
-  L.Vd = take(L.pipelined ? (size_t)ND * m * 8 : 1);  // ND x m x 16 words
+  L.Vd = take(L.pipelined ? (size_t)ND * m * 8 : 1);  // m x ND x 16 words
   L.dtotal = o;
   o = 0;
   L.pos = take(n);

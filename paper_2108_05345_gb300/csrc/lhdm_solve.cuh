@@ -980,11 +980,15 @@ struct Engine {
         unsigned sg, nb2;
         sign2(nega, negb, sg, nb2);
         if ((lane & 1) == 0) {
-          // word lane/2 of the row; its 16-byte chunk is stored XOR-swizzled
-          // by row, as the commit's shared-memory digit planes expect
-          const int w = lane >> 1, wp = ((((w >> 2) ^ (row >> 1)) & 3) << 2) | (w & 3);
+          // a row holds its ND digit planes (16 words each) side by side;
+          // 16-byte chunk c of the row is stored at c ^ (row & 7), as the
+          // commit's shared-memory layout expects
+          const int w = lane >> 1;
 #pragma unroll
-          for (int k = 0; k < ND; ++k) I.Vd[((size_t)k * I.m + row) * 16 + wp] = dig2k(k, ha, la, hb, lb, sg, nb2);
+          for (int k = 0; k < ND; ++k) {
+            const int c = (4 * k + (w >> 2)) ^ (row & 7);
+            I.Vd[(size_t)row * (16 * ND) + c * 4 + (w & 3)] = dig2k(k, ha, la, hb, lb, sg, nb2);
+          }
         }
         if (lane == 0) I.Ver[row] = er;
       }
@@ -1736,10 +1740,10 @@ struct Engine {
   //    and the trailing norm in FP64.
   // Every sum is exact or in a fixed order, so the result is bitwise
   // reproducible.  Shared memory (bytes of the work area): V digit buffers
-  // [0, 64K) and [64K, 128K) (ND planes of R rows x 64 B, 16-byte chunks
-  // XOR-swizzled by row so that ldmatrix is conflict-free), pass-1 C' digit
-  // buffers in the upper halves of those (pass 1 has R = 64), D' digits at
-  // 128K.
+  // [0, 64K) and [64K, 128K) (R rows of 512 B: the ND digit planes side by
+  // side, 16-byte chunks XOR-swizzled by row so that ldmatrix is
+  // conflict-free), pass-1 C' digit buffers in the upper halves of those
+  // (pass 1 has R = 64), D' digits at 128K.
   template <int NBP, int KT>
   __device__ bool commit_tc(const CommitShape& cs, int nb) {
     constexpr int NTN = NBP / 8;           // column tiles
@@ -1754,15 +1758,16 @@ struct Engine {
     unsigned short* sE = sV + 2 * BUF;
     __shared__ int s_Ec[CB], s_Ee[CB];
     const int g = lane >> 2, tq = lane & 3;
-    // digit plane k of a chunk of R rows: R x 32 bf16, 16-byte chunk q of
-    // row r at chunk q ^ ((r >> 1) & 3)
-    auto vaddr = [&](const unsigned short* base, int R, int k, int r, int q) {
-      return base + (k * R + r) * 32 + ((q ^ ((r >> 1) & 3)) << 3);
+    // digit k, 16-byte chunk q (reflectors 8q .. 8q+7) of staged row r:
+    // rows of 512 bytes, chunk 4k + q at (4k + q) ^ (r & 7)
+    auto vaddr = [&](const unsigned short* base, int, int k, int r, int q) {
+      return base + r * (16 * ND * 2) + (((4 * k + q) ^ (r & 7)) << 3);
     };
-    // V digits of rows rb .. rb+R into buffer b: one bulk copy per digit
-    // plane (the rows are stored pre-swizzled), completing on the buffer's
-    // mbarrier; rows past L are zeroed by the threads.  Every thread orders
-    // its earlier generic writes of the work area before the async copies.
+    // V digits of rows rb .. rb+R into buffer b: one bulk copy (the rows are
+    // stored pre-swizzled), completing on the buffer's mbarrier; rows past L
+    // are zeroed by the threads.  Every thread orders
+    // its generic writes of the work area before later async copies (proxy
+    // fence at entry, before pass 2 and after zeroing).
     __shared__ unsigned long long s_mbar[2];
     unsigned vph = 0u;  // bit b: parity of buffer b's next phase
     fence_proxy_async();
@@ -1776,16 +1781,14 @@ struct Engine {
       unsigned short* dst = sV + b * BUF;
       const int nr = min(R, L - rb);
       if (tid == 0) {
-        mbar_expect_tx(&s_mbar[b], (unsigned)(ND * nr * 64));
-        for (int k = 0; k < ND; ++k)
-          bulk_g2s(dst + k * R * 32, I.Vd + ((size_t)k * I.m + rb) * 16, (unsigned)(nr * 64), &s_mbar[b]);
+        mbar_expect_tx(&s_mbar[b], (unsigned)(nr * 64 * ND));
+        bulk_g2s(dst, I.Vd + (size_t)rb * (16 * ND), (unsigned)(nr * 64 * ND), &s_mbar[b]);
       }
-      const int zq = (R - nr) * 4;  // 16-byte chunks past L per plane
-      for (int e = tid; e < ND * zq; e += NT) {
-        const int k = e / zq, rem = e - k * zq;
-        *reinterpret_cast<uint4*>(dst + (k * R + nr) * 32 + rem * 8) = make_uint4(0u, 0u, 0u, 0u);
+      if (nr < R) {
+        for (int e = nr * 4 * ND + tid; e < R * 4 * ND; e += NT)
+          *reinterpret_cast<uint4*>(dst + e * 8) = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async();
       }
-      fence_proxy_async();
     };
     // wait for buffer b's copies (bounded); false on expiry
     auto wait_v = [&](int b) -> bool {
