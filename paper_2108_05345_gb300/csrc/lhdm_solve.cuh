@@ -1872,15 +1872,18 @@ struct Engine {
 #pragma unroll
       for (int k = 0; k < ND; ++k) *reinterpret_cast<unsigned*>(sBb + (k * NBP + dc) * SB + drr) = dig2k(k, ha, la, hb, lb, sg, nb2);
     };
+    // levels 0 .. NEX-1 move every 128 rows into exact int32 sums in shared
+    // memory (shared atomics: exact, so the order of the warps does not
+    // matter); levels NEX .. 8 stay in FP32, where their rounding weighs
+    // below 2^-54 of the scales
+    constexpr int NEX = 7;
+    int* sF = reinterpret_cast<int*>(reinterpret_cast<char*>(sV) + 131072);  // COMBOS x NEX x 32 x 4
+    for (int e = tid; e < COMBOS * NEX * 128; e += NT) sF[e] = 0;
     float acc[NLV][4];
-    int iacc[NLV][4];
 #pragma unroll
     for (int l = 0; l < NLV; ++l)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        acc[l][j] = 0.f;
-        iacc[l][j] = 0;
-      }
+      for (int j = 0; j < 4; ++j) acc[l][j] = 0.f;
     int since = 0;
     // every CTA walks the chunks from its own starting chunk, so that the
     // CTAs do not all ask for the same digit rows at the same moment (the
@@ -1925,34 +1928,40 @@ struct Engine {
         digits_c(b ^ 1);
       }
       since += 16;
-      if (since == 128 || jc + 1 == nch1) {
+      if (mw && (since == 128 || jc + 1 == nch1)) {
 #pragma unroll
-        for (int l = 0; l < NLV; ++l)
+        for (int l = 0; l < NEX; ++l)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            iacc[l][j] += __float2int_rn(acc[l][j]);
+            atomicAdd(sF + ((cmb * NEX + l) * 32 + lane) * 4 + j, __float2int_rn(acc[l][j]));
             acc[l][j] = 0.f;
           }
-        since = 0;
       }
+      if (since == 128) since = 0;
     }
-    // sum over the sub-blocks (exact, int64) and D from the level sums
+    // levels NEX .. 8 summed over the sub-blocks in order, then D from the
+    // level sums
     __syncthreads();
-    int* sStage = reinterpret_cast<int*>(sV);                                     // MW x NLV x 32 x 4
+    float* sStage = reinterpret_cast<float*>(sV);                                 // MW x (NLV-NEX) x 32 x 4
     double* sL = reinterpret_cast<double*>(reinterpret_cast<char*>(sV) + 73728);  // NLV x 32 x NBP
     if (mw) {
 #pragma unroll
-      for (int l = 0; l < NLV; ++l)
+      for (int l = NEX; l < NLV; ++l)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sStage[((warp * NLV + l) * 32 + lane) * 4 + j] = iacc[l][j];
+        for (int j = 0; j < 4; ++j) sStage[((warp * (NLV - NEX) + l - NEX) * 32 + lane) * 4 + j] = acc[l][j];
     }
     __syncthreads();
     for (int e = tid; e < COMBOS * NLV * 128; e += NT) {
       const int j = e & 3, ln = (e >> 2) & 31, lam = (e >> 7) % NLV, cb = (e >> 7) / NLV;
-      long long v = 0;
-      for (int sb = 0; sb < 4; ++sb) v += sStage[(((sb * COMBOS + cb) * NLV + lam) * 32 + ln) * 4 + j];
+      double v = 0.0;
+      if (lam < NEX) {
+        v = (double)sF[((cb * NEX + lam) * 32 + ln) * 4 + j];
+      } else {
+        for (int sb = 0; sb < 4; ++sb)
+          v += (double)sStage[(((sb * COMBOS + cb) * (NLV - NEX) + lam - NEX) * 32 + ln) * 4 + j];
+      }
       const int t = (cb % KT) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb / KT) * 8 + 2 * (ln & 3) + (j & 1);
-      sL[(lam * 32 + t) * NBP + c] = (double)v;
+      sL[(lam * 32 + t) * NBP + c] = v;
     }
     __syncthreads();
     for (int o = tid; o < kp * nb; o += NT) {
@@ -2231,7 +2240,7 @@ struct Engine {
     }
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     // the tensor-core form needs this panel's reflector digits
-    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 65536;
+    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 16384;  // int32 level sums
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
       __syncthreads();
