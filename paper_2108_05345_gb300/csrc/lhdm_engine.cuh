@@ -330,10 +330,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* mb, unsigned p
       : "memory");
   return ok != 0;
 }
-// 2^e as a double (normal range) or via ldexp
-__device__ __forceinline__ double pow2d(int e) {
-  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
-  return ldexp(1.0, e);
+// 2^e as a double, e in the normal range [-1022, 1023]
+__device__ __forceinline__ double pow2n(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// x 2^e for |e| <= 2044 by one or two exact power-of-two multiplications
+// (only a result in the subnormal range is rounded)
+__device__ __forceinline__ double scale2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * pow2n(e);
+  const int e1 = e / 2;
+  return (x * pow2n(e1)) * pow2n(e - e1);
 }
 
 // ---------------------------------------------------------------- teams

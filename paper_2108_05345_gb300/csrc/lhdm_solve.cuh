@@ -2059,7 +2059,8 @@ struct Engine {
             for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
-            const double x = fma(-(double)u, pow2d(((j < 2) ? er0 : er1) + ((j & 1) ? ee1 : ee0) - 57), xv[j]);
+            const int es = max(-2044, ((j < 2) ? er0 : er1) + ((j & 1) ? ee1 : ee0) - 57);
+            const double x = xv[j] - scale2((double)u, es);
             p[row] = x;
             if (row >= kp) {
               if (j & 1) nrm1 = fma(x, x, nrm1);
