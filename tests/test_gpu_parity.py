@@ -115,6 +115,24 @@ def test_ragged_shapes(L, ctx, shape, k_max):
     assert_parity(x, P, info, ref, ctx=ctx)
 
 
+@pytest.mark.parametrize("rr,cc,k_max", [(6, 0, 12), (6, 0, 32), (4, 4, 32)])
+def test_badly_scaled_rows_and_columns(L, ctx, rr, cc, k_max):
+    """Rows scaled by 2^-rr .. 2^rr and columns by 2^-cc .. 2^cc: the blocked
+    commit cuts its operands into digits under row and column scales, so
+    magnitudes that differ by thousands within one product are its hardest
+    case (the scaling itself is exact)."""
+    A, b, _ = WL.overdetermined_uniform(5, m=700, n=350)
+    rng = np.random.default_rng(11)
+    rs = 2.0 ** rng.integers(-rr, rr + 1, size=A.shape[0])
+    cs = 2.0 ** rng.integers(-cc, cc + 1, size=A.shape[1])
+    A = A * rs[:, None] * cs[None, :]
+    b = b * rs
+    x, P, _, info = solve(L, ctx, A, b, k_max=k_max)
+    ref = O.nnls(A, b, k_max=k_max, trace=True)
+    assert ref["status"] == 0
+    assert_parity(x, P, info, ref, ctx=ctx)
+
+
 def test_empty_problems(L, ctx):
     for (m, n) in [(0, 5), (5, 0), (0, 0)]:
         A = np.zeros((m, n))
