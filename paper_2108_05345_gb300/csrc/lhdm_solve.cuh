@@ -2002,9 +2002,6 @@ struct Engine {
     const bool act2 = warp < 8 * NTN;
     const int rt = warp & 7, nt2 = warp >> 3;
     const int c0 = nt2 * 8 + 2 * tq;
-    double* colp0 = (act2 && c0 < nb) ? commit_col(cs.s_cid, c0) : nullptr;
-    double* colp1 = (act2 && c0 + 1 < nb) ? commit_col(cs.s_cid, c0 + 1) : nullptr;
-    const int ee0 = s_Ee[c0], ee1 = s_Ee[c0 + 1];
     double nrm0 = 0.0, nrm1 = 0.0;
     const int s2 = tm.rank % nch2;
     auto row2 = [&](int jc) { return ((jc + s2) % nch2) * R2; };
@@ -2023,10 +2020,11 @@ struct Engine {
         // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
         const int ra = rb + rt * 16 + g, rb8 = ra + 8;
         double xv[4];
-        xv[0] = (colp0 && ra < L) ? ldcg(colp0 + ra) : 0.0;
-        xv[1] = (colp1 && ra < L) ? ldcg(colp1 + ra) : 0.0;
-        xv[2] = (colp0 && rb8 < L) ? ldcg(colp0 + rb8) : 0.0;
-        xv[3] = (colp1 && rb8 < L) ? ldcg(colp1 + rb8) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + (j & 1), row = (j < 2) ? ra : rb8;
+          xv[j] = (act2 && c < nb && row < L) ? ldcg(commit_col(cs.s_cid, c) + row) : 0.0;
+        }
         const int er0 = (ra < L) ? ldcg(I.Ver + ra) : 0, er1 = (rb8 < L) ? ldcg(I.Ver + rb8) : 0;
         float a2[NLV][4];
 #pragma unroll
@@ -2052,14 +2050,15 @@ struct Engine {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int row = (j < 2) ? ra : rb8;
-          double* p = (j & 1) ? colp1 : colp0;
-          if (p && row < L) {
+          const int c = c0 + (j & 1);
+          if (c < nb && row < L) {
+            double* p = commit_col(cs.s_cid, c);
             long long u = 0;
 #pragma unroll
             for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
-            const int es = max(-2044, ((j < 2) ? er0 : er1) + ((j & 1) ? ee1 : ee0) - 57);
+            const int es = max(-2044, ((j < 2) ? er0 : er1) + s_Ee[c] - 57);
             const double x = xv[j] - scale2((double)u, es);
             p[row] = x;
             if (row >= kp) {
