@@ -19,6 +19,7 @@ import json
 import multiprocessing as mp
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -51,8 +52,7 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 ".bench_clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "lhdm_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
