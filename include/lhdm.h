@@ -103,13 +103,17 @@ int lhdm_default_params(lhdm_params* p);
 const char* lhdm_status_string(int status);
 
 /*
- * Creates a single-solve context for problems up to max_m x max_n on the
- * current CUDA device.  Allocates all device workspace here (FP64 about
+ * Creates a solve context on the current CUDA device for single problems up
+ * to max_m x max_n (lhdm_solve) and for batches of up to max_batch problems,
+ * each at most max_m x max_n (lhdm_solve_batched; max_batch = 0: no batched
+ * solves).  Allocates the single-solve workspace here (FP64, about
  * 8 * (max_m * max_n + min(max_m,max_n)^2) bytes plus O(max_m + max_n));
- * later solves allocate nothing.  *ctx receives the handle (host).
- * Errors: INVALID_ARG (sizes < 1 or ctx NULL), ALLOC, CUDA.
+ * later single solves allocate nothing.  The batch workspace is sized by the
+ * first lhdm_solve_batched call with a given set of instances (see there).
+ * *ctx receives the handle (host).
+ * Errors: INVALID_ARG (sizes < 1, max_batch < 0 or ctx NULL), ALLOC, CUDA.
  */
-int lhdm_create(lhdm_ctx** ctx, int32_t max_m, int32_t max_n);
+int lhdm_create(lhdm_ctx** ctx, int32_t max_m, int32_t max_n, int32_t max_batch);
 
 /* Releases the context and its device memory (synchronises the device). */
 int lhdm_destroy(lhdm_ctx* ctx);
@@ -184,18 +188,83 @@ int lhdm_solve_noalloc(int32_t m, int32_t n, const double* A, int32_t lda, const
 int lhdm_get_info(lhdm_ctx* ctx, lhdm_info* info, void* stream);
 
 /*
- * lhdm_backward: adjoint of the solution map of the last lhdm_solve on ctx,
- * on its final passive set P (x_P is the least-squares solution on P,
- * subproblem (6) of section 2.1).  With g = dL/dx it solves
- * R^T R u = g_P with the final R factor and writes
+ * lhdm_backward: adjoint of the solution map on the final passive set P of
+ * a solve on ctx (x_P is the least-squares solution on P, subproblem (6) of
+ * section 2.1; P is locally constant where the solution is strictly
+ * complementary).  With g = dL/dx it solves R^T R u = g_P with the final R
+ * factor and writes
  *     dL/db   = A_P u                          (length m)
  *     dL/dA_P = r u^T - (A_P u) x_P^T,  dL/dA_Z = 0   (m x n, ld ld_dA)
- * where r = b - A x.  dLdx (length n), dLdb, dLdA: device.  A must be the
- * matrix passed to the solve (lda as then).  Either output may be NULL.
- * Errors: NO_STATE (no completed solve), INVALID_ARG, CUDA.
+ * where r = b - A x.
+ *  idx   < 0: the last lhdm_solve on ctx (one cooperative launch over every
+ *        SM, asynchronous on stream);
+ *        >= 0: instance idx of the last lhdm_solve_batched on ctx (one CTA;
+ *        the call synchronises the stream).
+ *  A     device; the matrix passed to that solve (lda as then).
+ *  dLdx  device, length n.  dLdb (length m), dLdA (m x n, ld_dA >= m):
+ *        device; either may be NULL.
+ * Errors: NO_STATE (no completed solve of that kind), INVALID_ARG (idx out
+ * of range, pointers, ld_dA), CUDA.
  */
-int lhdm_backward(lhdm_ctx* ctx, const double* A, int32_t lda, const double* dLdx,
+int lhdm_backward(lhdm_ctx* ctx, int32_t idx, const double* A, int32_t lda, const double* dLdx,
                   double* dLdb, double* dLdA, int32_t ld_dA, void* stream);
+
+/*
+ * lhdm_solve_batched: `batch` independent problems of uneven sizes (paper
+ * problem (1) per instance, Algorithm 3 on each) in ONE persistent launch;
+ * each CTA takes instances from a device work queue, largest first.
+ *  batch          0 <= batch <= max_batch of the context.
+ *  m, n, lda      host arrays [batch]; m[i] <= max_m, n[i] <= max_n.
+ *  A, b, x, passive  host arrays [batch] of DEVICE pointers, shapes as in
+ *                 lhdm_solve (A[i] column-major m[i] x n[i], ld lda[i]).
+ *  prm            host, NULL = defaults; prm->k_max <= 0 takes k_max per
+ *                 instance from the autotuner's table (lhdm_batch_autotune).
+ *  info           DEVICE array of batch lhdm_info, one per instance.
+ * The first call with a given argument set (sizes, pointers, parameters)
+ * plans the batch: it allocates the batch workspace, uploads the instance
+ * table and synchronises the stream, so it cannot be captured in a CUDA
+ * graph.  Every later call with the same arguments reuses that plan and only
+ * enqueues one small reset and one kernel launch (no allocation, no host
+ * synchronisation): that call can be captured.  Different arguments replace
+ * the plan.  The per-instance state for lhdm_backward(idx >= 0) and
+ * lhdm_backward_batched lives in the plan until the next replacement.
+ * Errors: INVALID_ARG, ALLOC, CUDA.
+ */
+int lhdm_solve_batched(lhdm_ctx* ctx, int32_t batch, const int32_t* m, const int32_t* n,
+                       const double* const* A, const int32_t* lda, const double* const* b,
+                       const lhdm_params* prm, double* const* x, int32_t* const* passive,
+                       lhdm_info* info, void* stream);
+
+/*
+ * Adjoint of every instance of the last lhdm_solve_batched on ctx, one
+ * launch (formulas of lhdm_backward): host arrays [batch] of device pointers
+ * dLdx, dLdb, dLdA (entries may be NULL; a NULL dLdx[i] skips instance i)
+ * and host ld_dA[batch] (NULL: ld = m[i]).  Synchronises the stream.
+ * Errors: NO_STATE, INVALID_ARG, CUDA.
+ */
+int lhdm_backward_batched(lhdm_ctx* ctx, const double* const* dLdx, double* const* dLdb,
+                          double* const* dLdA, const int32_t* ld_dA, void* stream);
+
+/*
+ * Bound, in nanoseconds, on every wait of one CTA for another in the solves
+ * and adjoints launched on ctx after this call (the grid barrier, the flags
+ * of the pipelined triangular solve and of the rotation log); ns <= 0
+ * restores the default of 4 s.  When a wait runs out the waiting CTA sets an
+ * error flag, every CTA leaves the kernel without further waits, and the
+ * solve reports status LHDM_ERR_TIMEOUT; the context stays usable (the next
+ * call clears the barrier words).  Host only.  Errors: INVALID_ARG.
+ */
+int lhdm_set_wait_limit(lhdm_ctx* ctx, int64_t ns);
+
+/*
+ * Failure-detection test aid: the next lhdm_solve on ctx runs with a grid
+ * barrier that expects one arrival more than the grid has, so no CTA ever
+ * releases it, every CTA's bounded wait runs out (lhdm_set_wait_limit) and
+ * the solve reports LHDM_ERR_TIMEOUT.  Nothing faults or hangs: the kernel
+ * returns after the wait limit.  Later solves are unaffected.
+ * Errors: INVALID_ARG.
+ */
+int lhdm_debug_stall_next_solve(lhdm_ctx* ctx);
 
 /* Decision trace of the last solve (verification aid): up to max_rows rows
  * of 6 int32 per outer step, host buffer out[6 * max_rows]:

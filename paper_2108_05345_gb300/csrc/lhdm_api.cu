@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -45,6 +46,18 @@ struct lhdm_ctx {
   // state for the adjoint
   bool have_state = false;
   int last_m = 0, last_n = 0;
+  // bounded waits (0 = default) and the failure-detection test's stall
+  long long wait_ns = 0;
+  bool stall_next = false;
+  // batched solves: the plan of the last lhdm_solve_batched and the
+  // arguments it was made for (reused while they repeat)
+  int max_batch = 0;
+  lhdm_batch* plan = nullptr;
+  std::vector<int32_t> pm, pn, plda;
+  std::vector<const void*> pptr;  // A, b, x, passive of every instance, then info
+  lhdm_params pprm{};
+  bool batch_state = false;
+  int* d_zero = nullptr;  // one int 0: the work-queue order of a one-instance adjoint
 };
 
 struct lhdm_batch {
@@ -66,12 +79,20 @@ struct lhdm_batch {
   bool ran = false;
 };
 
-static bool g_attr_done = false;
+// Kernel attributes are per device context: a flag per device records that
+// they were set on it (set under a mutex, read without one).
+constexpr int MAX_DEVICES = 64;
+static std::mutex g_attr_mu;
+static std::atomic<bool> g_attr_done[MAX_DEVICES];
 
 static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LHDM_OK : LHDM_ERR_CUDA; }
 
 static int set_attrs() {
-  if (g_attr_done) return LHDM_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LHDM_ERR_CUDA;
+  if (g_attr_done[dev].load(std::memory_order_acquire)) return LHDM_OK;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_attr_done[dev].load(std::memory_order_relaxed)) return LHDM_OK;
   cudaError_t e = cudaFuncSetAttribute(lhdm_solve_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(lhdm_backward_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
@@ -80,7 +101,7 @@ static int set_attrs() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(lhdm_backward_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_SMEM);
   if (e != cudaSuccess) return LHDM_ERR_CUDA;
-  g_attr_done = true;
+  g_attr_done[dev].store(true, std::memory_order_release);
   return LHDM_OK;
 }
 
@@ -133,8 +154,8 @@ const char* lhdm_status_string(int s) {
   }
 }
 
-int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n) {
-  if (!out || max_m < 1 || max_n < 1) return LHDM_ERR_INVALID_ARG;
+int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n, int32_t max_batch) {
+  if (!out || max_m < 1 || max_n < 1 || max_batch < 0) return LHDM_ERR_INVALID_ARG;
   *out = nullptr;
   lhdm_ctx* c = new (std::nothrow) lhdm_ctx();
   if (!c) return LHDM_ERR_ALLOC;
@@ -153,6 +174,7 @@ int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n) {
   }
   c->max_m = max_m;
   c->max_n = max_n;
+  c->max_batch = max_batch;
   c->cap = std::max(std::min(max_m, max_n), 1);
   c->ldr = (c->cap + 1) & ~1;
   if ((max_n + c->nsm - 1) / c->nsm > CAND_LOCAL_MAX) { delete c; return LHDM_ERR_INVALID_ARG; }
@@ -173,6 +195,8 @@ int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n) {
   if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 2 * NPHASE * sizeof(double));
   c->trace_cap = 3 * max_n + 8;
   if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)6 * c->trace_cap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_zero, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_zero, 0, sizeof(int));
   if (e != cudaSuccess) {
     lhdm_destroy(c);
     return e == cudaErrorMemoryAllocation ? LHDM_ERR_ALLOC : LHDM_ERR_CUDA;
@@ -201,6 +225,8 @@ int lhdm_destroy(lhdm_ctx* c) {
   cudaFree(c->hb);
   cudaFree(c->hx);
   cudaFree(c->hp);
+  cudaFree(c->d_zero);
+  if (c->plan) lhdm_batch_destroy(c->plan);
   delete c;
   return LHDM_OK;
 }
@@ -219,6 +245,7 @@ static void fill_ctx_inst(lhdm_ctx* c, Inst& I) {
   I.phase_ns = c->d_phase;
   I.trace = c->d_trace;
   I.trace_cap = c->trace_cap;
+  I.wait_ns = c->wait_ns > 0 ? c->wait_ns : WAIT_NS;
 }
 
 int lhdm_solve(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
@@ -242,6 +269,8 @@ int lhdm_solve(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, 
   I.passive_out = passive;
   I.prm = to_dev(p);
   fill_ctx_inst(c, I);
+  I.bar_extra = c->stall_next ? 1 : 0;
+  c->stall_next = false;
   c->have_state = false;
   cudaError_t e = cudaMemsetAsync(c->bar, 0, 4 * sizeof(unsigned int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), st);
@@ -350,14 +379,35 @@ int lhdm_debug_state(lhdm_ctx* c, const char* name, void* host, int64_t count, v
   return LHDM_ERR_INVALID_ARG;
 }
 
-int lhdm_backward(lhdm_ctx* c, const double* A, int32_t lda, const double* dLdx, double* dLdb, double* dLdA,
-                  int32_t ld_dA, void* stream) {
+static int batch_adjoint(lhdm_batch* B, std::vector<BatchItem>& it, const int* d_perm, int count, int nblocks,
+                         cudaStream_t st);
+
+int lhdm_backward(lhdm_ctx* c, int32_t idx, const double* A, int32_t lda, const double* dLdx, double* dLdb,
+                  double* dLdA, int32_t ld_dA, void* stream) {
   if (!c) return LHDM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (idx >= 0) {
+    // one instance of the last batched solve: the batch adjoint kernel on a
+    // one-entry table, one CTA
+    if (!c->batch_state || !c->plan) return LHDM_ERR_NO_STATE;
+    lhdm_batch* B = c->plan;
+    if (idx >= B->batch) return LHDM_ERR_INVALID_ARG;
+    BatchItem it = B->items[idx];
+    const int m = it.m, n = it.n;
+    if ((m > 0 && n > 0 && A != it.A) || (n > 0 && !dLdx)) return LHDM_ERR_INVALID_ARG;
+    if (dLdA && ld_dA < std::max(1, m)) return LHDM_ERR_INVALID_ARG;
+    (void)lda;
+    it.g = dLdx;
+    it.dLdb = dLdb;
+    it.dLdA = dLdA;
+    it.ld_dA = ld_dA;
+    std::vector<BatchItem> one(1, it);
+    return batch_adjoint(B, one, c->d_zero, 1, 1, st);
+  }
   if (!c->have_state) return LHDM_ERR_NO_STATE;
   const int m = c->last_m, n = c->last_n;
   if ((m > 0 && n > 0 && !A) || lda < std::max(1, m) || (n > 0 && !dLdx)) return LHDM_ERR_INVALID_ARG;
   if (dLdA && ld_dA < std::max(1, m)) return LHDM_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
   Inst I;
   std::memset(&I, 0, sizeof(I));
   I.m = m;
@@ -376,6 +426,17 @@ int lhdm_backward(lhdm_ctx* c, const double* A, int32_t lda, const double* dLdx,
   return cuda_ok(e);
 }
 
+int lhdm_set_wait_limit(lhdm_ctx* c, int64_t ns) {
+  if (!c) return LHDM_ERR_INVALID_ARG;
+  c->wait_ns = ns > 0 ? (long long)ns : 0;
+  return LHDM_OK;
+}
+
+int lhdm_debug_stall_next_solve(lhdm_ctx* c) {
+  if (!c) return LHDM_ERR_INVALID_ARG;
+  c->stall_next = true;
+  return LHDM_OK;
+}
 
 // ----------------------------------------------------------------------- allocation-free solve
 // Callers that cannot allocate device memory (see lhdm_solve_noalloc) use one
@@ -396,7 +457,7 @@ struct NoallocDevice {
   size_t oR = 0, oxP = 0, oR2 = 0, oI = 0;  // word offsets
 };
 static std::mutex g_noalloc_mu;
-static NoallocDevice g_noalloc[64];
+static NoallocDevice g_noalloc[MAX_DEVICES];
 
 // Per-device set-up (first call on the device, with it current): the symbol's
 // device address, kernel attributes and the fixed workspace layout.
@@ -445,7 +506,7 @@ extern "C" int lhdm_solve_noalloc(int32_t m, int32_t n, const double* A, int32_t
   int rc = check_params(&p, false);
   if (rc) return rc;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LHDM_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LHDM_ERR_CUDA;
   NoallocDevice* d = &g_noalloc[dev];
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -654,16 +715,9 @@ int lhdm_batch_backward(lhdm_batch* B, const double* const* dLdx, double* const*
     it[i].ld_dA = ld_dA ? ld_dA[i] : std::max(1, it[i].m);
     if (it[i].dLdA && it[i].ld_dA < std::max(1, it[i].m)) return LHDM_ERR_INVALID_ARG;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  // the adjoint descriptors go to a second table so the forward table stays intact
-  cudaError_t e = cudaMemcpyAsync(B->d_adj, it.data(), B->batch * sizeof(BatchItem), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
-  if (e != cudaSuccess) return LHDM_ERR_CUDA;
-  lhdm_backward_batch_kernel<<<B->nblocks, NT, DYN_SMEM, st>>>(B->d_adj, B->d_perm, B->batch, B->d_queue, B->L,
-                                                                B->dscr, B->iscr);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return cuda_ok(e);
+  int rc = batch_adjoint(B, it, B->d_perm, B->batch, B->nblocks, (cudaStream_t)stream);
+  if (rc) return rc;
+  return cuda_ok(cudaStreamSynchronize((cudaStream_t)stream));
 }
 
 int lhdm_batch_kmax(const lhdm_batch* B, int32_t i) {
@@ -687,6 +741,87 @@ int lhdm_batch_destroy(lhdm_batch* B) {
 }
 
 }  // extern "C"
+
+// The adjoint kernel of a batch over the descriptors `it` (count entries,
+// visited in the order d_perm gives), on nblocks CTAs.  The descriptors go to
+// the plan's second table, so the forward table stays intact; the table is
+// uploaded from a host buffer that stays alive until the copy has run.
+static int batch_adjoint(lhdm_batch* B, std::vector<BatchItem>& it, const int* d_perm, int count, int nblocks,
+                         cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(B->d_adj, it.data(), count * sizeof(BatchItem), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `it` is a pageable host buffer
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return LHDM_ERR_CUDA;
+  lhdm_backward_batch_kernel<<<nblocks, NT, DYN_SMEM, st>>>(B->d_adj, d_perm, count, B->d_queue, B->L, B->dscr,
+                                                            B->iscr);
+  return cuda_ok(cudaGetLastError());
+}
+
+// lhdm_solve_batched: the batch plan of the context is made on the first call
+// with a given argument set and reused while the arguments repeat.
+static bool same_batch_args(const lhdm_ctx* c, int batch, const int32_t* m, const int32_t* n, const int32_t* lda,
+                            const double* const* A, const double* const* b, double* const* x,
+                            int32_t* const* passive, const lhdm_info* info, const lhdm_params& p) {
+  if (!c->plan || (int)c->pm.size() != batch) return false;
+  if (std::memcmp(&c->pprm, &p, sizeof(p)) != 0) return false;
+  for (int i = 0; i < batch; ++i) {
+    if (c->pm[i] != m[i] || c->pn[i] != n[i] || c->plda[i] != lda[i]) return false;
+    if (c->pptr[4 * i] != A[i] || c->pptr[4 * i + 1] != b[i] || c->pptr[4 * i + 2] != x[i] ||
+        c->pptr[4 * i + 3] != passive[i])
+      return false;
+  }
+  return c->pptr[4 * batch] == (const void*)info;
+}
+
+extern "C" int lhdm_solve_batched(lhdm_ctx* c, int32_t batch, const int32_t* m, const int32_t* n,
+                                  const double* const* A, const int32_t* lda, const double* const* b,
+                                  const lhdm_params* prm, double* const* x, int32_t* const* passive,
+                                  lhdm_info* info, void* stream) {
+  if (!c || batch < 0 || batch > c->max_batch) return LHDM_ERR_INVALID_ARG;
+  if (batch > 0 && (!m || !n || !A || !lda || !b || !x || !passive || !info)) return LHDM_ERR_INVALID_ARG;
+  for (int i = 0; i < batch; ++i)
+    if (m[i] > c->max_m || n[i] > c->max_n) return LHDM_ERR_INVALID_ARG;
+  lhdm_params p;
+  lhdm_default_params(&p);
+  if (prm) p = *prm;
+  int rc = check_params(&p, true);
+  if (rc) return rc;
+  if (!same_batch_args(c, batch, m, n, lda, A, b, x, passive, info, p)) {
+    if (c->plan) {
+      lhdm_batch_destroy(c->plan);
+      c->plan = nullptr;
+    }
+    c->batch_state = false;
+    c->pm.assign(m, m + batch);
+    c->pn.assign(n, n + batch);
+    c->plda.assign(lda, lda + batch);
+    c->pptr.resize(4 * (size_t)batch + 1);
+    for (int i = 0; i < batch; ++i) {
+      c->pptr[4 * i] = A[i];
+      c->pptr[4 * i + 1] = b[i];
+      c->pptr[4 * i + 2] = x[i];
+      c->pptr[4 * i + 3] = passive[i];
+    }
+    c->pptr[4 * batch] = info;
+    c->pprm = p;
+    rc = lhdm_batch_create(&c->plan, batch, m, n, lda, A, b, x, passive, info, &p, stream);
+    if (rc) {
+      c->plan = nullptr;
+      c->pm.clear();
+      return rc;
+    }
+  }
+  rc = lhdm_batch_run(c->plan, stream);
+  c->batch_state = rc == LHDM_OK;
+  return rc;
+}
+
+extern "C" int lhdm_backward_batched(lhdm_ctx* c, const double* const* dLdx, double* const* dLdb,
+                                     double* const* dLdA, const int32_t* ld_dA, void* stream) {
+  if (!c) return LHDM_ERR_INVALID_ARG;
+  if (!c->batch_state || !c->plan) return LHDM_ERR_NO_STATE;
+  return lhdm_batch_backward(c->plan, dLdx, dLdb, dLdA, ld_dA, stream);
+}
 
 extern "C" int lhdm_batch_autotune(int32_t batch, const int32_t* m, const int32_t* n, const int32_t* lda,
                                    const double* const* A, const double* const* b, const lhdm_params* prm,

@@ -9,7 +9,7 @@ __global__ void __launch_bounds__(NT, 1) lhdm_backward_grid_kernel(Inst I, unsig
                                                                    const double* g, double* dLdb,
                                                                    double* dLdA, int ld_dA, double* apu) {
   extern __shared__ double dyn[];
-  GridTeam tm{(int)blockIdx.x, (int)gridDim.x, bar, err};
+  GridTeam tm{(int)blockIdx.x, (int)gridDim.x, bar, err, I.wait_ns, I.bar_extra};
   Engine<GridTeam> e(tm, I, dyn);
   Adjoint<GridTeam> adj(e);
   adj.run(g, dLdb, dLdA, ld_dA, apu);

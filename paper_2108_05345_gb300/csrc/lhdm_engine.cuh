@@ -47,7 +47,7 @@ constexpr int INV_PARTS = TB / NW;   // column classes of a diagonal-block inver
 constexpr int DB = 32;               // downdate block (positions per warp)
 constexpr int NPHASE = 12;
 constexpr double EPS = 2.220446049250313e-16;  // 2^-52
-constexpr long long WAIT_NS = 4000000000LL;    // bound on any device-side wait
+constexpr long long WAIT_NS = 4000000000LL;    // default bound on any device-side wait
 
 enum Phase {
   PH_SETUP = 0, PH_DM, PH_PANEL, PH_SOLVE, PH_COMMIT, PH_INNER, PH_RESID, PH_DUAL,
@@ -112,6 +112,9 @@ struct Inst {
   double* phase_ns;           // NPHASE (may be null)
   int* trace;                 // 6 ints per outer step (may be null)
   int trace_cap;              // rows available in trace
+  long long wait_ns;          // bound on a wait for another CTA (ns)
+  int bar_extra;              // failure-detection test: arrivals the grid barrier
+                              // expects beyond the grid (0 in every normal solve)
   DevParams prm;
 };
 
@@ -342,13 +345,18 @@ __device__ __forceinline__ double scale2(double x, int e) {
 
 // ---------------------------------------------------------------- teams
 // Whole-grid team: one CTA per SM, co-resident (cooperative launch).  The
-// barrier is a generation counter; every wait is bounded by WAIT_NS and sets
-// *err on expiry, after which every CTA leaves the solve.
+// barrier is a generation counter; every wait is bounded by wait_ns and sets
+// *err on expiry, after which every CTA leaves the solve.  `extra` raises the
+// arrival count of the main barrier beyond the grid: only the
+// failure-detection test sets it, so that no CTA ever releases the barrier and
+// every wait runs out.
 struct GridTeam {
   int rank, size;
   unsigned int* bar;  // [0] arrivals, [1] generation; [2], [3] the same for sub-teams
   int* err;
-  __device__ __forceinline__ bool sync() { return sync_words(bar, size); }
+  long long wait_ns;
+  int extra;
+  __device__ __forceinline__ bool sync() { return sync_words(bar, size + extra); }
   // barrier of ranks 0 .. n-1 only (the other ranks must not call it)
   __device__ __forceinline__ bool sync_sub(int n) { return sync_words(bar + 2, n); }
   __device__ __forceinline__ bool sync_words(unsigned int* bw, int n) {
@@ -373,7 +381,7 @@ struct GridTeam {
         while (*gen == g) {
           if ((++spins & 63u) == 0u) {
             if (*(volatile int*)err) { ok = 0; break; }
-            if (gtimer() - t0 > WAIT_NS) { atomicExch(err, 1); ok = 0; break; }
+            if (gtimer() - t0 > wait_ns) { atomicExch(err, 1); ok = 0; break; }
           }
         }
       }
@@ -398,14 +406,14 @@ struct CtaTeam {
 };
 
 // Bounded wait until *flag >= target (one thread); false on timeout.
-__device__ __forceinline__ bool wait_ge(const int* flag, int target, int* err) {
+__device__ __forceinline__ bool wait_ge(const int* flag, int target, int* err, long long wait_ns) {
   if (*(volatile const int*)flag >= target) return true;
   const long long t0 = gtimer();
   unsigned int spins = 0;
   while (*(volatile const int*)flag < target) {
     if ((++spins & 63u) == 0u) {
       if (err && *(volatile int*)err) return false;
-      if (gtimer() - t0 > WAIT_NS) {
+      if (gtimer() - t0 > wait_ns) {
         if (err) atomicExch(err, 1);
         return false;
       }

@@ -132,6 +132,8 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.Vd = L.pipelined ? reinterpret_cast<unsigned*>(d + L.Vd) : nullptr;
   I.Ver = L.pipelined ? ip + L.Ver : nullptr;
   I.amask = nullptr;
+  I.wait_ns = WAIT_NS;
+  I.bar_extra = 0;
 }
 
 inline __device__ void bind_item(Inst& I, const BatchItem& it) {

@@ -1246,7 +1246,7 @@ struct Engine {
         // the stale columns of this block are being inverted by the last
         // ranks in this call: wait for them instead of substituting
         int okw = 1;
-        if (tid < INV_PARTS) okw = wait_ge(ifl + bi * INV_PARTS + tid, ep, tm_err()) ? 1 : 0;
+        if (tid < INV_PARTS) okw = wait_ge(ifl + bi * INV_PARTS + tid, ep, tm_err(), I.wait_ns) ? 1 : 0;
         if (!__syncthreads_and(okw)) return false;
         v = nbk;
       } else {
@@ -1293,7 +1293,7 @@ struct Engine {
       int okw = 1;
       double acc = 0.0;
       if (g == 0 && row < nbk && bi + 2 < nb) {
-        okw = wait_ge(sfl + (b0 + row) / SLAB, ep, tm_err()) ? 1 : 0;
+        okw = wait_ge(sfl + (b0 + row) / SLAB, ep, tm_err(), I.wait_ns) ? 1 : 0;
         if (okw) acc = ldcg(I.accb + b0 + row);
       }
       if (!__syncthreads_and(okw)) return false;
@@ -1382,7 +1382,7 @@ struct Engine {
         const double v0 = (j0 < nc) ? ldcg(Rcol(sl0) + r0 + row) : 0.0;
         const double v1 = (j1 < nc) ? ldcg(Rcol(sl1) + r0 + row) : 0.0;
         int okw = 1;
-        if (tid == 0) okw = wait_ge(yfl + c, ep, tm_err()) ? 1 : 0;
+        if (tid == 0) okw = wait_ge(yfl + c, ep, tm_err(), I.wait_ns) ? 1 : 0;
         if (!__syncthreads_and(okw)) return false;
         const double y0 = (j0 < nc) ? ldcg(I.yP + c0 + j0) : 0.0;
         const double y1 = (j1 < nc) ? ldcg(I.yP + c0 + j1) : 0.0;
@@ -2483,7 +2483,7 @@ struct Engine {
               if (lane == 0) {
                 int* er = tm_err();
                 bad = (er && *(volatile int*)er) ? 1 : 0;
-                if (!bad && gtimer() - tw0 > WAIT_NS) {
+                if (!bad && gtimer() - tw0 > I.wait_ns) {
                   if (er) atomicExch(er, 1);
                   bad = 1;
                 }
@@ -2633,7 +2633,7 @@ struct Engine {
             if (lane == 0) {
               int* er = tm_err();
               bad = (er && *(volatile int*)er) ? 1 : 0;
-              if (!bad && gtimer() - tw0 > WAIT_NS) {
+              if (!bad && gtimer() - tw0 > I.wait_ns) {
                 if (er) atomicExch(er, 1);
                 bad = 1;
               }
@@ -2670,7 +2670,7 @@ struct Engine {
             if (lane == 0) {
               int* er = tm_err();
               bad = (er && *(volatile int*)er) ? 1 : 0;
-              if (!bad && gtimer() - tw0 > WAIT_NS) {
+              if (!bad && gtimer() - tw0 > I.wait_ns) {
                 if (er) atomicExch(er, 1);
                 bad = 1;
               }

@@ -63,13 +63,15 @@ def lib():
         L.lhdm_default_params.argtypes = [P]
         L.lhdm_status_string.argtypes = [C.c_int]
         L.lhdm_status_string.restype = C.c_char_p
-        L.lhdm_create.argtypes = [C.POINTER(V), i32, i32]
+        L.lhdm_create.argtypes = [C.POINTER(V), i32, i32, i32]
         L.lhdm_destroy.argtypes = [V]
         L.lhdm_solve.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
         L.lhdm_solve_host.argtypes = [V, i32, i32, d, i32, d, P, d, d, I, V]
         L.lhdm_solve_noalloc.argtypes = [i32, i32, d, i32, d, P, d, d, d, V]
         L.lhdm_get_info.argtypes = [V, I, V]
-        L.lhdm_backward.argtypes = [V, d, i32, d, d, d, i32, V]
+        L.lhdm_backward.argtypes = [V, i32, d, i32, d, d, d, i32, V]
+        L.lhdm_set_wait_limit.argtypes = [V, C.c_int64]
+        L.lhdm_debug_stall_next_solve.argtypes = [V]
         L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
         L.lhdm_trace.argtypes = [V, C.POINTER(C.c_int32), i32, V]
         L.lhdm_debug_state.argtypes = [V, C.c_char_p, C.c_void_p, C.c_int64, V]
@@ -78,6 +80,8 @@ def lib():
         L.lhdm_batch_create.argtypes = [C.POINTER(V), i32, ip, ip, ip, pp, pp, pp, pp, d, P, V]
         L.lhdm_batch_run.argtypes = [V, V]
         L.lhdm_batch_backward.argtypes = [V, pp, pp, pp, ip, V]
+        L.lhdm_solve_batched.argtypes = [V, i32, ip, ip, pp, ip, pp, P, pp, pp, d, V]
+        L.lhdm_backward_batched.argtypes = [V, pp, pp, pp, ip, V]
         L.lhdm_batch_kmax.argtypes = [V, i32]
         L.lhdm_batch_destroy.argtypes = [V]
         L.lhdm_batch_autotune.argtypes = [i32, ip, ip, ip, pp, pp, P, ip, V]
@@ -157,14 +161,24 @@ def info_from_device(buf):
     return Info.from_buffer_copy(buf.cpu().numpy().tobytes()).as_dict()
 
 
-class Context:
-    """A solve context for problems up to max_m x max_n (lhdm_create)."""
+def _ptrs(ts):
+    return (C.c_void_p * max(len(ts), 1))(*[t.data_ptr() if t is not None else None for t in ts])
 
-    def __init__(self, max_m, max_n):
+
+def _ints(vals):
+    return (C.c_int32 * max(len(vals), 1))(*vals)
+
+
+class Context:
+    """A solve context (lhdm_create) for single problems up to max_m x max_n
+    and batches of up to max_batch such problems."""
+
+    def __init__(self, max_m, max_n, max_batch=0):
         h = C.c_void_p()
-        _check(lib().lhdm_create(C.byref(h), int(max_m), int(max_n)), "lhdm_create")
+        _check(lib().lhdm_create(C.byref(h), int(max_m), int(max_n), int(max_batch)), "lhdm_create")
         self.h = h
-        self.max_m, self.max_n = int(max_m), int(max_n)
+        self.max_m, self.max_n, self.max_batch = int(max_m), int(max_n), int(max_batch)
+        self._batch_keep = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -190,6 +204,51 @@ class Context:
                               C.byref(info) if info is not None else None, _stream(stream))
         _check(rc, "lhdm_solve")
         return x, passive, (info.as_dict() if info is not None else None)
+
+    def solve_batched(self, As, bs, params=None, xs=None, ps=None, infos=None, stream=None):
+        """lhdm_solve_batched: one persistent launch over the instances (lists
+        of column-major (m_i, n_i) tensors and length-m_i vectors).  Returns
+        (xs, passives, infos) with infos a device float64 buffer of the
+        per-instance lhdm_info records (info_list() decodes it).  Passing the
+        same tensors again reuses the context's plan (capturable)."""
+        k = len(As)
+        dev = As[0].device if k else torch.device("cuda")
+        if xs is None:
+            xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A in As]
+        if ps is None:
+            ps = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in As]
+        if infos is None:
+            infos = torch.zeros(max(k, 1) * C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
+        m = _ints([A.shape[0] for A in As])
+        n = _ints([A.shape[1] for A in As])
+        lda = _ints([_lda(A) for A in As])
+        for b, A in zip(bs, As):
+            if b.dtype != torch.float64 or b.numel() != A.shape[0] or not b.is_contiguous():
+                raise ValueError("every b must be a contiguous float64 vector of its A's row count")
+        rc = lib().lhdm_solve_batched(self.h, k, m, n, _ptrs(As), lda, _ptrs(bs),
+                                      C.byref(params) if params is not None else None,
+                                      _ptrs(xs), _ptrs(ps), infos.data_ptr(), _stream(stream))
+        _check(rc, "lhdm_solve_batched")
+        self._batch_keep = (As, bs, xs, ps, infos)
+        return xs, ps, infos
+
+    @staticmethod
+    def info_list(infos, count):
+        raw = infos.cpu().numpy().tobytes()
+        sz = C.sizeof(Info)
+        return [Info.from_buffer_copy(raw[i * sz:(i + 1) * sz]).as_dict() for i in range(count)]
+
+    def backward_batched(self, As, dLdx, want_db=True, want_dA=True, stream=None):
+        """lhdm_backward_batched for the last solve_batched; returns lists
+        (dL/db, dL/dA) (column-major dL/dA)."""
+        dbs = [torch.empty(A.shape[0], dtype=torch.float64, device=A.device) for A in As] if want_db else None
+        dAs = [colmajor(torch.empty(A.shape, dtype=torch.float64, device=A.device)) for A in As] if want_dA else None
+        gs = [g.contiguous() if g is not None else None for g in dLdx]
+        ld = _ints([max(1, A.shape[0]) for A in As])
+        rc = lib().lhdm_backward_batched(self.h, _ptrs(gs), _ptrs(dbs) if dbs else None,
+                                         _ptrs(dAs) if dAs else None, ld, _stream(stream))
+        _check(rc, "lhdm_backward_batched")
+        return dbs, dAs
 
     def solve_host(self, A, b, params=None, stream=None):
         """lhdm_solve_host on host arrays (numpy, Fortran order or any layout
@@ -221,17 +280,24 @@ class Context:
         _check(lib().lhdm_get_info(self.h, C.byref(inf), _stream(stream)), "lhdm_get_info")
         return inf.as_dict()
 
-    def backward(self, A, dLdx, want_db=True, want_dA=True, stream=None):
-        """lhdm_backward for the last solve; returns (dL/db, dL/dA)."""
+    def backward(self, A, dLdx, want_db=True, want_dA=True, idx=-1, stream=None):
+        """lhdm_backward: adjoint of the last solve (idx < 0) or of instance
+        idx of the last solve_batched; returns (dL/db, dL/dA)."""
         m, n = A.shape
         lda = _lda(A)
         db = torch.empty(m, dtype=torch.float64, device=A.device) if want_db else None
         dA = colmajor(torch.empty(m, n, dtype=torch.float64, device=A.device)) if want_dA else None
-        rc = lib().lhdm_backward(self.h, A.data_ptr(), lda, dLdx.contiguous().data_ptr(),
+        rc = lib().lhdm_backward(self.h, int(idx), A.data_ptr(), lda, dLdx.contiguous().data_ptr(),
                                  db.data_ptr() if db is not None else None,
                                  dA.data_ptr() if dA is not None else None, max(1, m), _stream(stream))
         _check(rc, "lhdm_backward")
         return db, dA
+
+    def set_wait_limit(self, ns):
+        _check(lib().lhdm_set_wait_limit(self.h, int(ns)), "lhdm_set_wait_limit")
+
+    def stall_next_solve(self):
+        _check(lib().lhdm_debug_stall_next_solve(self.h), "lhdm_debug_stall_next_solve")
 
     def trace(self, stream=None):
         """Per outer step: |J| from DM, |J| kept, inner steps, |P| after,

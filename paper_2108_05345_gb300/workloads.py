@@ -54,21 +54,29 @@ def sparse_recovery_sweep(seed, s, m=2048, n=8192):
     return gaussian_recovery(m, n, s, seed + 7919 * s, unit_columns=True)
 
 
+def batched_sizes(batch_seed=0, count=1024, m_lo=64, m_hi=512):
+    """Row counts m_i of the batched uneven workload (n_i = 2 m_i)."""
+    return [int(m) for m in np.random.default_rng(batch_seed).integers(m_lo, m_hi + 1, size=count)]
+
+
+def batched_instance(i, m, density=0.1, noise_var=1e-3):
+    """Instance i of the batched uneven workload at m rows: n = 2m,
+    A ~ N(0, 1/m), x0 with density*n nonzeros uniform on (0.1, 1],
+    b = A x0 + N(0, noise_var); drawn from seed 1000 + i."""
+    n = 2 * m
+    rng = np.random.default_rng(1000 + i)
+    A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+    x0 = _sparse_nonneg(rng, n, max(1, int(round(density * n))))
+    b = A @ x0 + rng.normal(0.0, np.sqrt(noise_var), size=m)
+    return np.asfortranarray(A), b, x0
+
+
 def batched_uneven(batch_seed=0, count=1024, m_lo=64, m_hi=512, density=0.1, noise_var=1e-3):
     """`count` independent instances, m ~ U{m_lo..m_hi}, n = 2m, A ~ N(0, 1/m),
     x0 with density*n nonzeros uniform on (0.1, 1], b = A x0 + N(0, noise_var).
     Instance i is drawn from seed 1000 + i; its size from the batch seed."""
-    sizes = np.random.default_rng(batch_seed).integers(m_lo, m_hi + 1, size=count)
-    out = []
-    for i, m in enumerate(sizes):
-        m = int(m)
-        n = 2 * m
-        rng = np.random.default_rng(1000 + i)
-        A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
-        x0 = _sparse_nonneg(rng, n, max(1, int(round(density * n))))
-        b = A @ x0 + rng.normal(0.0, np.sqrt(noise_var), size=m)
-        out.append((np.asfortranarray(A), b, x0))
-    return out
+    sizes = batched_sizes(batch_seed, count, m_lo, m_hi)
+    return [batched_instance(i, m, density, noise_var) for i, m in enumerate(sizes)]
 
 
 def layer_batch(count=256, m=512, n=1024, s=40, noise_var=1e-3, seed0=0):
@@ -93,3 +101,25 @@ def tiny(seed, m, n, kind="gauss"):
     A = rng.normal(size=(m, n)) if kind == "gauss" else rng.uniform(size=(m, n))
     b = rng.normal(size=m)
     return np.asfortranarray(A), b
+
+
+def dependent_triple(m=12, n=8, seed=0):
+    """A small instance whose first DM block contains a column that is the
+    sum of two others: a_1 and a_4 orthonormal (random directions), a_6 =
+    a_1 + a_4 (rounded once), the other columns small Gaussian (norm about
+    0.1), b = 1.2 a_1 + a_4.  Returns A, b and the indices (i1, i2, i3) with
+    a_i3 = a_i1 + a_i2."""
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, 0.1 / np.sqrt(m), size=(m, n))
+    Q, _ = np.linalg.qr(rng.normal(size=(m, 2)))
+    A[:, 1] = Q[:, 0]
+    A[:, 4] = Q[:, 1]
+    A[:, 6] = A[:, 1] + A[:, 4]
+    b = 1.2 * A[:, 1] + A[:, 4]
+    return np.asfortranarray(A), b, (1, 4, 6)
+
+
+def with_duplicate(A, c, at):
+    """A with an exact copy of column c inserted at index `at`."""
+    A2 = np.insert(np.asarray(A), at, np.asarray(A)[:, c], axis=1)
+    return np.asfortranarray(A2)

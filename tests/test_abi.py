@@ -42,8 +42,12 @@ def test_host_only_validation(lib):
     assert (p.tau1, p.tau2, p.delta, p.k_max) == (0.6, 0.15, 0.9, 32)
     assert L.lhdm_default_params(None) == lhdm.LHDM_ERR_INVALID_ARG
     h = C.c_void_p()
-    assert L.lhdm_create(C.byref(h), 0, 5) == lhdm.LHDM_ERR_INVALID_ARG
-    assert L.lhdm_create(None, 5, 5) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_create(C.byref(h), 0, 5, 0) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_create(C.byref(h), 5, 5, -1) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_create(None, 5, 5, 0) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_solve_batched(None, 0, None, None, None, None, None, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_backward_batched(None, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_set_wait_limit(None, 5) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_solve(None, 1, 1, None, 1, None, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_destroy(None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_batch_run(None, None) == lhdm.LHDM_ERR_INVALID_ARG

@@ -334,3 +334,61 @@ def test_adjoint_closed_form_vs_finite_differences():
         assert abs(fd - dLdA[i, j]) <= 1e-5 * max(1.0, abs(fd)), (i, j, fd, dLdA[i, j])
     Z = [j for j in range(n) if j not in P]
     assert not dLdA[:, Z].any()
+
+
+# ---------------------------------------------------------------- rank guard
+@pytest.mark.parametrize("seed", range(4))
+def test_rank_guard_truncates_dependent_block(seed):
+    """A DM block {a6, a1, a4} with a6 = a1 + a4 (a1, a4 orthonormal; pairwise
+    cosines 1/sqrt(2) and 0, all below delta = 0.9, so Algorithm 2 accepts all
+    three).  With b = 1.2 a1 + a4 = a6 + 0.2 a1: w = A^T b gives w6 = 2.2 (the
+    argmax), w1 = 1.2, w4 = 1.0, so with tau1 = 0.4 both are candidates, in
+    that order.  After the reflectors of a6 and a1 the trailing part of a4 is
+    at the rounding level: the rank guard (a column whose trailing norm is
+    <= 100 eps ||a_j|| cannot enter) ends J there, so two columns are
+    appended, y = (1, 0.2) > 0 (no drop), the residual is zero and the solve
+    stops after one outer step with x6 = 1, x1 = 0.2.  Appending the third
+    column (the guard skipped) puts a rounding-level pivot into R and moves
+    the solution to another point of the optimal set."""
+    A, b, (i1, i2, i3) = WL.dependent_triple(seed=seed)
+    w = A.T @ b
+    assert np.argmax(w) == i3 and sorted(np.argsort(-w)[:3].tolist()) == sorted([i1, i2, i3])
+    r = O.nnls(A, b, k_max=8, tau1=0.4, trace=True)
+    assert r["status"] == O.OK
+    assert r["trace"][0].tolist() == [3, 2, 0, 2, 0, i3]
+    assert r["n_drop"] == 0
+    assert r["n_outer"] == 1 and r["passive"].tolist() == sorted([i1, i3])
+    expect = np.zeros(A.shape[1])
+    expect[i3], expect[i1] = 1.0, 0.2
+    np.testing.assert_allclose(r["x"], expect, rtol=0, atol=1e-14)
+    # the optimum value is zero (b lies in the cone of the columns)
+    assert r["resid_norm"] <= 1e-14
+    res_bf, _, _ = brute_force_nnls(A, b)
+    assert res_bf <= 1e-14
+
+
+@pytest.mark.parametrize("k_max", [1, 4])
+@pytest.mark.parametrize("where", ["after", "before"])
+def test_duplicate_column_takes_lowest_index(k_max, where):
+    """An exact copy of a passive column: the two copies tie in every
+    comparison (w and the trailing norm), the argmax tie rule picks the
+    lower index, and once it is passive the copy's trailing part is zero, so
+    it never enters.  The solution is the one of the original matrix with
+    the coefficient on the lower-indexed copy, the optimum value unchanged
+    (brute force agrees)."""
+    for seed in range(6):
+        A, b = WL.tiny(seed, 12, 8)
+        base = O.nnls(A, b, k_max=k_max)
+        P = base["passive"].tolist()
+        c = P[0]
+        at = A.shape[1] if where == "after" else c  # copy after all, or just before c
+        A2 = WL.with_duplicate(A, c, at)
+        r = O.nnls(A2, b, k_max=k_max)
+        assert r["status"] == O.OK
+        x_expect = np.insert(base["x"], at, 0.0)
+        if where == "before":  # the copy now has the lower index: it carries the coefficient
+            x_expect[at], x_expect[c + 1] = base["x"][c], 0.0
+        np.testing.assert_allclose(r["x"], x_expect, rtol=0, atol=1e-12 * max(1.0, np.abs(base["x"]).max()))
+        both = {at, c if where == "after" else c + 1}
+        assert not both <= set(r["passive"].tolist())
+        assert abs(r["resid_norm"] - base["resid_norm"]) <= 1e-12 * max(1.0, np.linalg.norm(b))
