@@ -41,6 +41,12 @@
  *    step (rank guard, n > m); a J column whose trailing norm falls below the
  *    same bound after the earlier J reflectors ends J there.
  *  - max_outer (default 3n) caps the outer loop.
+ *  - positivity trick ([A -A], section 3.2): the twin of a passive column is
+ *    not in Z (its projection is zero in exact arithmetic).  Sign flip
+ *    (section 4.2): every passive column with y < 0 is replaced by its twin,
+ *    whose R column is the negated one (so y changes sign there and nowhere
+ *    else) and whose previous iterate is 0 (it was in Z); an exact zero of y
+ *    left after the flips goes through the ordinary inner step.
  *
  * Parity: pinned (see the not-gpu tests): KKT, brute-force enumeration,
  * scipy's nnls, closed forms, exact recovery, hand-built DM cases, the
@@ -65,10 +71,15 @@ typedef struct {
   int k_max;
   double tol_w;   /* < 0: default */
   int max_outer;  /* <= 0: 3n */
+  int twin_n;     /* > 0: the matrix is [A  -A] (section 3.2, the positivity
+                     trick) with n = 2 twin_n; column j's twin is j +- twin_n */
+  int sign_flip;  /* with twin_n: the sign flip of section 4.2 replaces the
+                     inner loop's downdate for negative y (Algorithm LH's
+                     inner loop otherwise) */
 } orc_params;
 
 typedef struct {
-  int status, n_outer, n_inner, n_drop, n_passive, rank_limited;
+  int status, n_outer, n_inner, n_drop, n_passive, rank_limited, n_flip;
   double resid_norm, max_wZ, tol_w;
 } orc_info;
 
@@ -263,6 +274,24 @@ static void state_solve(const orc_state* s, double* y) {
 }
 
 /*
+ * Sign flip (section 4.2) at position p of the positivity-trick matrix
+ * [A -A]: column k = order[p] is replaced by its twin kb, whose R column is
+ * the negated R column of k (Q is unchanged, since Q^T(-a_k) = -Q^T a_k);
+ * k returns to Z with W(:, k) = Q^T a_k = [R column; 0], as held.
+ */
+static void state_flip(orc_state* s, int p, int twin_n) {
+  const int m = s->m;
+  const int k = s->order[p];
+  const int kb = k < twin_n ? k + twin_n : k - twin_n;
+  const double* wk = s->W + (size_t)k * m;
+  double* wb = s->W + (size_t)kb * m;
+  for (int i = 0; i < m; ++i) wb[i] = (i < s->nP) ? -wk[i] : 0.0;
+  s->order[p] = kb;
+  s->pos[kb] = p;
+  s->pos[k] = -1;
+}
+
+/*
  * Algorithm 2 (Deviation Maximization) on the columns cols[0..ncols) of a
  * column-major matrix C (ld ldc), using rows [row0, row0+L).  w and u are
  * indexed by the entries of cols.  Writes the ordered J (entries of cols)
@@ -331,6 +360,13 @@ static int dm_select_core(int L, int row0, int ncols, const int* cols,
   }
   free(I); free(Kc); free(G); free(d); free(Jpos);
   return nJ;
+}
+
+/* With the positivity trick, is column j's twin passive? */
+static int twin_passive(const orc_state* s, int j, int twin_n) {
+  if (twin_n <= 0) return 0;
+  const int jb = j < twin_n ? j + twin_n : j - twin_n;
+  return s->pos[jb] >= 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -440,6 +476,12 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
   if (inf.status) { if (info) *info = inf; return inf.status; }
 
   const int k_max = prm->k_max;
+  const int twin_n = prm->twin_n;
+  if (twin_n < 0 || (twin_n > 0 && n != 2 * twin_n)) {
+    inf.status = ORC_ERR_INVALID_ARG;
+    if (info) *info = inf;
+    return inf.status;
+  }
   orc_state* s = state_new(m, n, A, lda, b, k_max);
   double* w = (double*)malloc(sizeof(double) * (size_t)n);
   double* u = (double*)malloc(sizeof(double) * (size_t)n);
@@ -477,7 +519,7 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
     int ne = 0;
     double wz_any = -INFINITY;
     for (int j = 0; j < n; ++j) {
-      if (s->pos[j] >= 0) continue;
+      if (s->pos[j] >= 0 || twin_passive(s, j, twin_n)) continue;
       if (w[j] > wz_any) wz_any = w[j];
       if (u[j] > 100.0 * ORC_EPS * anorm[j]) elig[ne++] = j;
     }
@@ -528,6 +570,23 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
       state_solve(s, y);
     }
     inf.n_drop += drops;
+    /* sign flip (positivity trick, section 4.2): a passive column with
+       y < 0 gives way to its twin; y keeps its values up to that sign */
+    if (twin_n > 0 && prm->sign_flip) {
+      int flips = 0;
+      for (int p = 0; p < s->nP; ++p) {
+        const int k = s->order[p];
+        if (y[k] < 0.0) {
+          const int kb = k < twin_n ? k + twin_n : k - twin_n;
+          state_flip(s, p, twin_n);
+          x[kb] = 0.0;  /* the twin was in Z: its previous iterate is 0 */
+          x[k] = 0.0;
+          ++flips;
+        }
+      }
+      if (flips) state_solve(s, y);
+      inf.n_flip += flips;
+    }
     /* inner loop */
     int inner = 0, removed = 0;
     for (;;) {
@@ -611,7 +670,7 @@ int orc_nnls(int m, int n, const double* A, int lda, const double* b,
   inf.resid_norm = sqrt(col_dot(r, r, m));
   inf.max_wZ = -INFINITY;
   for (int j = 0; j < n; ++j)
-    if (s->pos[j] < 0) {
+    if (s->pos[j] < 0 && !twin_passive(s, j, twin_n)) {
       const double wj = col_dot(A + (size_t)j * lda, r, m);
       if (wj > inf.max_wZ) inf.max_wZ = wj;
     }

@@ -16,12 +16,14 @@ OK, INVALID_ARG, MAX_ITER, NONFINITE = 0, 1, 2, 4
 
 class _Params(C.Structure):
     _fields_ = [("tau1", C.c_double), ("tau2", C.c_double), ("delta", C.c_double),
-                ("k_max", C.c_int), ("tol_w", C.c_double), ("max_outer", C.c_int)]
+                ("k_max", C.c_int), ("tol_w", C.c_double), ("max_outer", C.c_int),
+                ("twin_n", C.c_int), ("sign_flip", C.c_int)]
 
 
 class _Info(C.Structure):
     _fields_ = [("status", C.c_int), ("n_outer", C.c_int), ("n_inner", C.c_int),
                 ("n_drop", C.c_int), ("n_passive", C.c_int), ("rank_limited", C.c_int),
+                ("n_flip", C.c_int),
                 ("resid_norm", C.c_double), ("max_wZ", C.c_double), ("tol_w", C.c_double)]
 
 
@@ -57,7 +59,7 @@ def _ip(a):
 
 
 def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
-         trace=False, want_R=False):
+         trace=False, want_R=False, twin_n=0, sign_flip=False):
     """Solve min ||Ax-b|| s.t. x >= 0 by LH (k_max=1) or LHDM (k_max>1).
 
     Returns a dict: x, order (ordered passive set), passive (sorted), info
@@ -70,7 +72,7 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
     m, n = A.shape
     x = np.zeros(n)
     order = np.full(n, -1, dtype=np.int32)
-    prm = _Params(tau1, tau2, delta, int(k_max), tol_w, int(max_outer))
+    prm = _Params(tau1, tau2, delta, int(k_max), tol_w, int(max_outer), int(twin_n), int(bool(sign_flip)))
     inf = _Info()
     cap = 4 * n + 8 if trace else 0
     ti = np.zeros(6 * max(cap, 1), dtype=np.int32)
@@ -83,7 +85,7 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
     out = dict(x=x, order=order[:nP].copy(), passive=np.sort(order[:nP]), status=inf.status,
                n_outer=inf.n_outer, n_inner=inf.n_inner, n_drop=inf.n_drop, n_passive=nP,
                rank_limited=inf.rank_limited, resid_norm=inf.resid_norm, max_wZ=inf.max_wZ,
-               tol_w=inf.tol_w)
+               tol_w=inf.tol_w, n_flip=inf.n_flip)
     if trace:
         no = min(inf.n_outer, cap)
         out["trace"] = ti[: 6 * no].reshape(no, 6).copy()
@@ -92,6 +94,16 @@ def nnls(A, b, k_max=1, tau1=0.6, tau2=0.15, delta=0.9, tol_w=-1.0, max_outer=0,
     if want_R:
         out["R"] = R[: nP * nP].reshape(nP, nP, order="F").copy()
     return out
+
+
+def nnls_signed(A, b, sign_flip=False, **kw):
+    """Signed least squares through the positivity trick (section 3.2): NNLS
+    on the explicit matrix [A  -A], x = (x+, x-) of length 2n; with
+    sign_flip, the inner loop's downdate for a negative y is replaced by the
+    sign flip of section 4.2.  Returns the dict of nnls()."""
+    A = np.asarray(A, dtype=np.float64)
+    A2 = np.asfortranarray(np.hstack([A, -A]))
+    return nnls(A2, b, twin_n=A.shape[1], sign_flip=sign_flip, **kw)
 
 
 def dm_select(C_, w, u, tau1, tau2, delta, k_max):

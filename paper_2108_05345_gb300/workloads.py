@@ -123,3 +123,64 @@ def with_duplicate(A, c, at):
     """A with an exact copy of column c inserted at index `at`."""
     A2 = np.insert(np.asarray(A), at, np.asarray(A)[:, c], axis=1)
     return np.asfortranarray(A2)
+
+
+def _conditioned(rng, m, n, kappa):
+    """m x n matrix U diag(sigma) V^T with orthonormal U (m x r), V (n x r),
+    r = min(m, n), singular values log-spaced from 1 down to 1/kappa, then
+    columns scaled to unit norm (which moves the condition number a little;
+    the generated value is of the order of kappa)."""
+    r = min(m, n)
+    U, _ = np.linalg.qr(rng.normal(size=(m, r)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, r)))
+    sigma = np.logspace(0.0, -np.log10(kappa), r)
+    A = (U * sigma) @ V.T
+    A /= np.linalg.norm(A, axis=0, keepdims=True)
+    return A
+
+
+def conditioned_overdetermined(seed, m=2048, n=1024, kappa=1e6, noise_var=1e-4):
+    """Ill-conditioned dense NNLS (the paper's conditioned experiment, section
+    5, with condition numbers 1e5 - 1e6): A = U diag(sigma) V^T with unit-norm
+    columns, x_true with half its entries zero and the rest uniform on
+    (0, 1], b = A x_true + N(0, noise_var)."""
+    rng = np.random.default_rng(seed + 104729 * int(round(np.log10(kappa))))
+    A = _conditioned(rng, m, n, kappa)
+    x = np.zeros(n)
+    nz = rng.choice(n, size=n - n // 2, replace=False)
+    x[nz] = 1.0 - rng.uniform(0.0, 1.0, size=nz.size)
+    b = A @ x + rng.normal(0.0, np.sqrt(noise_var), size=m)
+    return np.asfortranarray(A), b, x
+
+
+def conditioned_recovery(seed, m=512, n=1024, s=32, kappa=1e6):
+    """Sparse nonnegative recovery with an ill-conditioned A (section 5): A as
+    in conditioned_overdetermined (underdetermined), x0 >= 0 with s nonzeros
+    uniform on (0.1, 1], b = A x0 (noiseless)."""
+    rng = np.random.default_rng(seed + 7919 * s + 104729 * int(round(np.log10(kappa))))
+    A = _conditioned(rng, m, n, kappa)
+    x0 = _sparse_nonneg(rng, n, s)
+    return np.asfortranarray(A), A @ x0, x0
+
+
+def signed_recovery(seed, m=256, n=512, s=25, unit_columns=False):
+    """Signed sparse recovery (the positivity-trick experiments of section 5):
+    A ~ N(0, 1/m) (or unit-norm Gaussian columns), x0 with s nonzeros of
+    random sign and magnitude uniform on (0.1, 1], b = A x0 (noiseless)."""
+    rng = np.random.default_rng(seed + 31337)
+    A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+    if unit_columns:
+        A /= np.linalg.norm(A, axis=0, keepdims=True)
+    x0 = _sparse_nonneg(rng, n, s)
+    x0 *= np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    return np.asfortranarray(A), A @ x0, x0
+
+
+def signed_overdetermined(seed, m=700, n=350, noise_var=1e-2):
+    """Signed least squares, overdetermined: A ~ N(0, 1/m), x_true ~ N(0, 1),
+    b = A x_true + N(0, noise_var)."""
+    rng = np.random.default_rng(seed + 4242)
+    A = rng.normal(0.0, 1.0 / np.sqrt(m), size=(m, n))
+    x = rng.normal(size=n)
+    b = A @ x + rng.normal(0.0, np.sqrt(noise_var), size=m)
+    return np.asfortranarray(A), b, x

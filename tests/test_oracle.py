@@ -392,3 +392,103 @@ def test_duplicate_column_takes_lowest_index(k_max, where):
         both = {at, c if where == "after" else c + 1}
         assert not both <= set(r["passive"].tolist())
         assert abs(r["resid_norm"] - base["resid_norm"]) <= 1e-12 * max(1.0, np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------- conditioned workload
+@pytest.mark.parametrize("kappa", [1e5, 1e6])
+def test_conditioned_problem_matches_scipy(kappa):
+    """Ill-conditioned overdetermined NNLS (condition numbers 1e5 - 1e6 as in
+    the paper's conditioned experiment): the minimiser is unique (full column
+    rank), so the oracle and scipy's independent active-set solver must agree
+    to the conditioning-limited accuracy, with the same support."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    A, b, _ = WL.conditioned_overdetermined(0, m=512, n=256, kappa=kappa)
+    assert 0.3 * kappa < np.linalg.cond(A) < 3 * kappa
+    xs, _ = scipy_opt.nnls(A, b, maxiter=50 * 256)
+    for k in (1, 16):
+        r = O.nnls(A, b, k_max=k)
+        assert r["status"] == O.OK
+        assert np.linalg.norm(r["x"] - xs) <= 1e-10 * np.linalg.norm(xs)
+        assert set(r["passive"].tolist()) == set(np.flatnonzero(xs > 0).tolist())
+        assert_kkt(A, b, r)
+
+
+@pytest.mark.parametrize("kappa", [1e5, 1e6])
+def test_conditioned_sparse_recovery(kappa):
+    """Noiseless sparse nonnegative recovery with an ill-conditioned A: x0 is
+    recovered (the paper reports LHDM solving every such instance)."""
+    for s in (16, 32):
+        A, b, x0 = WL.conditioned_recovery(0, s=s, kappa=kappa)
+        r = O.nnls(A, b, k_max=32)
+        assert r["status"] == O.OK
+        assert np.linalg.norm(r["x"] - x0) <= 1e-10 * np.linalg.norm(x0)
+        sig = np.flatnonzero(r["x"] > 1e-9 * r["x"].max()).tolist()
+        assert sig == np.flatnonzero(x0).tolist()
+
+
+# ---------------------------------------------------------------- positivity trick
+@pytest.mark.parametrize("flip", [False, True])
+@pytest.mark.parametrize("k_max", [1, 8])
+def test_positivity_trick_is_least_squares(flip, k_max):
+    """Section 3.2: NNLS on [A -A] reaches every signed vector, so for a full
+    column rank A (m > n) its optimum is the least-squares solution:
+    x+ - x- = lstsq(A, b) and the optimal residuals agree.  The twin rule
+    keeps at most one column of each pair passive (x+ * x- = 0)."""
+    for seed in range(3):
+        A, b, _ = WL.signed_overdetermined(seed, m=120, n=60)
+        r = O.nnls_signed(A, b, sign_flip=flip, k_max=k_max)
+        assert r["status"] == O.OK
+        n = A.shape[1]
+        xp, xm = r["x"][:n], r["x"][n:]
+        ls = np.linalg.lstsq(A, b, rcond=None)[0]
+        assert np.linalg.norm((xp - xm) - ls) <= 1e-11 * np.linalg.norm(ls)
+        assert not (xp * xm).any()
+        assert xp.min() >= 0 and xm.min() >= 0
+        assert abs(r["resid_norm"] - np.linalg.norm(A @ ls - b)) <= 1e-12 * np.linalg.norm(b)
+        if flip:
+            assert r["n_flip"] > 0 or r["n_inner"] == 0
+
+
+def test_sign_flip_replaces_inner_loop():
+    """Section 4.2: with the positivity trick the sign flip takes the place of
+    the inner loop's downdates (each flip keeps y up to one sign), so on the
+    same instance the flip variant runs no (or fewer) inner steps, flips
+    instead, and reaches the same optimum."""
+    A, b, _ = WL.signed_overdetermined(1, m=200, n=100)
+    r_in = O.nnls_signed(A, b, sign_flip=False, k_max=1)
+    r_fl = O.nnls_signed(A, b, sign_flip=True, k_max=1)
+    assert r_in["n_inner"] > 0 and r_in["n_flip"] == 0
+    assert r_fl["n_flip"] > 0 and r_fl["n_inner"] < r_in["n_inner"]
+    n = A.shape[1]
+    d_in = r_in["x"][:n] - r_in["x"][n:]
+    d_fl = r_fl["x"][:n] - r_fl["x"][n:]
+    assert np.linalg.norm(d_in - d_fl) <= 1e-11 * np.linalg.norm(d_in)
+
+
+@pytest.mark.parametrize("flip", [False, True])
+def test_positivity_trick_signed_recovery(flip):
+    """Noiseless signed sparse recovery: x+ = max(x0, 0), x- = max(-x0, 0)."""
+    for seed in range(4):
+        A, b, x0 = WL.signed_recovery(seed)
+        r = O.nnls_signed(A, b, sign_flip=flip, k_max=8)
+        n = A.shape[1]
+        expect = np.concatenate([np.maximum(x0, 0), np.maximum(-x0, 0)])
+        assert r["status"] == O.OK
+        assert np.linalg.norm(r["x"] - expect) <= 1e-10 * np.linalg.norm(expect)
+        # at a zero residual, columns with rounding-level coefficients may
+        # stay passive: the significant part is the support of x0
+        sig = np.flatnonzero(r["x"] > 1e-9 * r["x"].max()).tolist()
+        assert sig == np.flatnonzero(expect).tolist()
+        assert set(sig) <= set(r["passive"].tolist())
+
+
+def test_positivity_trick_brute_force():
+    """Tiny underdetermined cases (m = 6, n = 4, so [A -A] is 6 x 8): the
+    oracle's optimum equals brute-force enumeration on the explicit [A -A]."""
+    for seed in range(10):
+        A, b = WL.tiny(seed, 6, 4)
+        A2 = np.hstack([A, -A])
+        res_bf, _, _ = brute_force_nnls(A2, b)
+        for flip in (False, True):
+            r = O.nnls_signed(A, b, sign_flip=flip, k_max=4)
+            assert abs(r["resid_norm"] - res_bf) <= 1e-10 * max(1.0, np.linalg.norm(b))
