@@ -54,6 +54,14 @@ extern "C" {
 /* Largest supported block size k_max (columns chosen per outer step). */
 #define LHDM_KMAX_LIMIT 64
 
+/* Problem modes (lhdm_params.mode). */
+#define LHDM_MODE_NNLS 0        /* min ||A x - b||, x >= 0 (problem (1))        */
+#define LHDM_MODE_SIGNED 1      /* positivity trick, problem (positivity_trick)
+                                   of section 3.2: NNLS on [A  -A] without
+                                   forming -A; x = (x+, x-) has 2n entries     */
+#define LHDM_MODE_SIGNED_FLIP 2 /* the same, with the sign flip of section 4.2
+                                   in place of the inner loop's downdates      */
+
 /*
  * Algorithm parameters (Algorithm 2 and Algorithm 3).
  *  tau1, tau2 in (0, 1]: candidate thresholds on the dual vector w and on
@@ -66,8 +74,15 @@ extern "C" {
  *      "max w > 0" of Algorithms 1 and 3 with a floating-point tolerance);
  *      tol_w < 0 selects 10 * 2^-52 * max(m,n) * max_j ||a_j|| * ||b||.
  *  max_outer: cap on outer iterations; <= 0 selects 3n.
+ *  mode: LHDM_MODE_NNLS, LHDM_MODE_SIGNED or LHDM_MODE_SIGNED_FLIP.  In the
+ *      signed modes the problem is NNLS on the m x 2n matrix [A  -A]: A is
+ *      still passed as m x n, x and passive have 2n entries (x_j for column
+ *      j, x_{n+j} for column -a_j), and n stands for 2n in the defaults of
+ *      tol_w and max_outer.  The adjoint (lhdm_backward) is not available
+ *      for the signed modes.
+ *  reserved: set to 0.
  * Defaults (lhdm_default_params): tau1 = 0.6, tau2 = 0.15, delta = 0.9,
- * k_max = 32, the values of section 5.
+ * k_max = 32, the values of section 5; mode = LHDM_MODE_NNLS.
  */
 typedef struct {
   double tau1;
@@ -76,6 +91,8 @@ typedef struct {
   double tol_w;
   int32_t k_max;
   int32_t max_outer;
+  int32_t mode;
+  int32_t reserved;
 } lhdm_params;
 
 /* Per-solve report. */
@@ -88,6 +105,8 @@ typedef struct {
   int32_t n_passive;    /* |P| at exit                                       */
   int32_t rank_limited; /* 1 if columns with w > tol_w were left out because
                            their trailing norm was <= 100 eps ||a_j||        */
+  int32_t n_flip;       /* sign flips (LHDM_MODE_SIGNED_FLIP)                */
+  int32_t mode;         /* the mode solved                                   */
   double resid_norm;    /* ||b - A x||                                       */
   double max_wZ;        /* max over Z of w = A^T (b - A x) at exit           */
   double tol_w;         /* tolerance actually used                           */
@@ -125,8 +144,10 @@ int lhdm_destroy(lhdm_ctx* ctx);
  *  A           device, m x n, column-major, leading dimension lda.
  *  b           device, length m.
  *  prm         host; NULL selects the defaults.
- *  x           device, length n: the solution (x_Z = 0).
- *  passive     device, length n: the passive set P sorted ascending, then -1.
+ *  x           device, length n (2n in the signed modes): the solution
+ *              (x_Z = 0).
+ *  passive     device, length n (2n in the signed modes): the passive set P
+ *              sorted ascending, then -1.
  *  info        host or NULL.  When non-NULL the call synchronises the stream
  *              and fills it; when NULL the call is asynchronous and
  *              lhdm_get_info() retrieves the report later.

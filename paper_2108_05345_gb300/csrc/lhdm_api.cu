@@ -112,6 +112,7 @@ static int check_params(const lhdm_params* p, bool allow_auto_k) {
   if (std::isnan(p->tol_w)) return LHDM_ERR_INVALID_ARG;
   if (p->k_max > LHDM_KMAX_LIMIT) return LHDM_ERR_INVALID_ARG;
   if (p->k_max < 1 && !allow_auto_k) return LHDM_ERR_INVALID_ARG;
+  if (p->mode < LHDM_MODE_NNLS || p->mode > LHDM_MODE_SIGNED_FLIP) return LHDM_ERR_INVALID_ARG;
   return LHDM_OK;
 }
 
@@ -123,6 +124,7 @@ static DevParams to_dev(const lhdm_params& p) {
   d.tol_w = p.tol_w;
   d.k_max = p.k_max;
   d.max_outer = p.max_outer;
+  d.mode = p.mode;
   return d;
 }
 
@@ -136,6 +138,8 @@ int lhdm_default_params(lhdm_params* p) {
   p->tol_w = -1.0;
   p->k_max = 32;
   p->max_outer = 0;
+  p->mode = LHDM_MODE_NNLS;
+  p->reserved = 0;
   return LHDM_OK;
 }
 
@@ -278,7 +282,7 @@ int lhdm_solve(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, 
   void* args[] = {(void*)&I, (void*)&c->bar, (void*)&c->err};
   e = cudaLaunchCooperativeKernel((const void*)lhdm_solve_grid_kernel, dim3(c->nsm), dim3(NT), args, DYN_SMEM, st);
   if (e != cudaSuccess) return LHDM_ERR_CUDA;
-  c->have_state = true;
+  c->have_state = p.mode == LHDM_MODE_NNLS;  // the adjoint covers problem (1) only
   c->last_m = m;
   c->last_n = n;
   if (info) {
@@ -298,8 +302,8 @@ int lhdm_solve_host(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t 
   if (!c->hA) {
     e = cudaMalloc(&c->hA, (size_t)c->L.ldw * std::max(c->max_n, 1) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->hb, (size_t)std::max(c->max_m, 1) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&c->hx, (size_t)std::max(c->max_n, 1) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&c->hp, (size_t)std::max(c->max_n, 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->hx, (size_t)2 * std::max(c->max_n, 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->hp, (size_t)2 * std::max(c->max_n, 1) * sizeof(int));
     if (e != cudaSuccess) return LHDM_ERR_ALLOC;
   }
   const int ld = c->L.ldw;
@@ -310,9 +314,10 @@ int lhdm_solve_host(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t 
   if (e != cudaSuccess) return LHDM_ERR_CUDA;
   int rc = lhdm_solve(c, m, n, c->hA, ld, c->hb, prm, c->hx, c->hp, nullptr, stream);
   if (rc) return rc;
+  const size_t nx = (size_t)n * ((prm && prm->mode != LHDM_MODE_NNLS) ? 2 : 1);
   if (n > 0) {
-    e = cudaMemcpyAsync(x, c->hx, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(passive, c->hp, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(x, c->hx, nx * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(passive, c->hp, nx * sizeof(int), cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, c->d_info, sizeof(lhdm_info), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -389,7 +394,7 @@ int lhdm_backward(lhdm_ctx* c, int32_t idx, const double* A, int32_t lda, const 
   if (idx >= 0) {
     // one instance of the last batched solve: the batch adjoint kernel on a
     // one-entry table, one CTA
-    if (!c->batch_state || !c->plan) return LHDM_ERR_NO_STATE;
+    if (!c->batch_state || !c->plan || c->plan->prm.mode != LHDM_MODE_NNLS) return LHDM_ERR_NO_STATE;
     lhdm_batch* B = c->plan;
     if (idx >= B->batch) return LHDM_ERR_INVALID_ARG;
     BatchItem it = B->items[idx];
@@ -705,7 +710,7 @@ int lhdm_batch_run(lhdm_batch* B, void* stream) {
 int lhdm_batch_backward(lhdm_batch* B, const double* const* dLdx, double* const* dLdb, double* const* dLdA,
                         const int32_t* ld_dA, void* stream) {
   if (!B || (B->batch > 0 && !dLdx)) return LHDM_ERR_INVALID_ARG;
-  if (!B->ran) return LHDM_ERR_NO_STATE;
+  if (!B->ran || B->prm.mode != LHDM_MODE_NNLS) return LHDM_ERR_NO_STATE;
   if (B->batch == 0) return LHDM_OK;
   std::vector<BatchItem> it = B->items;
   for (int i = 0; i < B->batch; ++i) {

@@ -9,6 +9,15 @@
 // team; control decisions are recomputed identically by every CTA from data
 // published before the last barrier, so all CTAs follow the same path.
 //
+// Positivity trick (section 3.2, NNLS on [A -A] with x = (x+, x-)): the team
+// solves it on the n physical columns.  A passive column carries a sign
+// (csign): +1 stands for column j of [A -A], -1 for its twin n + j.  Since
+// Q^T(-a) = -Q^T a and a Householder reflector built from -x equals the one
+// built from x, R, W, y and x are kept for the physical columns and the signs
+// enter only where a sign is tested: the dual value of the pair is |w_j|
+// (index j if w_j >= 0, else n + j), y and x of column n + j are -y_j, -x_j.
+// The twin of a passive column is not in Z.
+//
 // State of an instance (section 2.1, whole-matrix variant of section 4.1):
 //   W  = Q^T A for the columns in Z (the B and C blocks), m x n, ld ldw;
 //        columns in P are not kept current in W - their R column is in R.
@@ -57,6 +66,8 @@ enum Phase {
 struct DevParams {
   double tau1, tau2, delta, tol_w;
   int k_max, max_outer;
+  int mode;  // LHDM_MODE_*: 0 plain NNLS; 1, 2 the positivity trick on [A -A]
+             // (2: with the sign flip of section 4.2 in the inner loop)
 };
 
 // Everything a team needs for one instance.  Persistent fields (R, rslot,
@@ -102,6 +113,8 @@ struct Inst {
   int* ipart;     // team.size x 8
   int* ctl;       // 16 ints of control words
   int* qlist;     // cap: positions removed by the current inner step
+  int* csign;     // n: positivity trick, sign of a passive column (+1: column j
+                  // of [A -A], -1: its twin n + j); unused otherwise
   double* Dinv;   // ceil(cap/TB) x TB x TB inverses of R's diagonal blocks (null: no pipelined solve)
   double* accb;   // ceil(cap/TB) x TB slab accumulations of the pipelined solve
   int* tflag;     // ceil(cap/TB) block flags, ceil(cap/TB) * TB/SLAB slab flags, ceil(cap/TB) * INV_PARTS inverse flags
@@ -119,7 +132,7 @@ struct Inst {
 };
 
 // control words (ctl[])
-enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK };
+enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK, C_NFLIP };
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }

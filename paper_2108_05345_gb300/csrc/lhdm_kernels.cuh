@@ -42,7 +42,7 @@ struct ScratchLayout {
   size_t Dinv, accb;  // pipelined triangular solve (teams of more than one CTA)
   size_t dtotal;
   size_t Vd;  // reflector digits (teams of more than one CTA)
-  size_t pos, J, candi, candn, ipart, ctl, qlist, tflag, Ver;
+  size_t pos, J, candi, candn, ipart, ctl, qlist, tflag, Ver, csign;
   size_t itotal;
   int ldw;
   bool pipelined;
@@ -94,6 +94,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.qlist = take(cap);
   L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB + INV_PARTS) : 1);
   L.Ver = take(L.pipelined ? m : 1);
+  L.csign = take(n);
   L.itotal = o;
   return L;
 }
@@ -126,6 +127,7 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.ipart = ip + L.ipart;
   I.ctl = ip + L.ctl;
   I.qlist = ip + L.qlist;
+  I.csign = ip + L.csign;
   I.Dinv = L.pipelined ? d + L.Dinv : nullptr;
   I.accb = L.pipelined ? d + L.accb : nullptr;
   I.tflag = L.pipelined ? ip + L.tflag : nullptr;

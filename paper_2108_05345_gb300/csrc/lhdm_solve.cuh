@@ -41,6 +41,9 @@ struct Engine {
   int kdm = 0, removed = 0, inner_step = 0;
   int inv_valid = 0;  // positions whose diagonal-block inverse column is current
   int tepoch = 0;     // pipelined-solve calls in this launch (flag values)
+  int sgn = 0;        // I.prm.mode: 0 plain NNLS, 1 positivity trick, 2 with sign flip
+  int nx = 0;         // columns of the problem solved: n, or 2n for [A -A]
+  int n_flip = 0;     // sign flips (mode 2)
 
   // phase timing (rank 0, thread 0)
   long long t_last = 0;
@@ -54,6 +57,8 @@ struct Engine {
     tid = threadIdx.x;
     lane = tid & 31;
     warp = tid >> 5;
+    sgn = I.prm.mode;
+    nx = sgn ? 2 * I.n : I.n;
     __shared__ double s_phf[2 * NPHASE];
     phf = s_phf;
     if (tid == 0)
@@ -82,6 +87,14 @@ struct Engine {
       return false;
     }
     return true;
+  }
+
+  // Positivity trick: the index in [A -A] of physical column c when its dual
+  // value is w, the physical column of an index, and the sign of position p.
+  __device__ __forceinline__ int ext_of(int c, double w) const { return (sgn && w < 0.0) ? c + I.n : c; }
+  __device__ __forceinline__ int phys(int e) const { return e >= I.n ? e - I.n : e; }
+  __device__ __forceinline__ double pos_sign(int p) const {
+    return sgn ? (double)ldcg(I.csign + ldcg(I.order + p)) : 1.0;
   }
 
   __device__ __forceinline__ double* Rcol(int slot) const { return I.R + (size_t)slot * I.ldr; }
@@ -180,10 +193,11 @@ struct Engine {
         const int pc = ldcg(I.pos + c);
         const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
         if (pc >= 0) continue;
-        wz = fmax(wz, wc);
+        const double wa = sgn ? fabs(wc) : wc;  // the better twin's dual value
+        wz = fmax(wz, wa);
         if (uc > (100.0 * EPS) * an) {
           ++ne;
-          best = amax_merge(best, ArgMax{wc, c});
+          best = amax_merge(best, ArgMax{wa, ext_of(c, wc)});
           um = fmax(um, uc);
         }
       }
@@ -280,7 +294,8 @@ struct Engine {
   __device__ bool dm_select(int* s_J) {
     const int km = I.prm.k_max;
     const int kc_max = km - 1;
-    if (tid == 0) s_J[0] = jsel;
+    const int jp = phys(jsel);
+    if (tid == 0) s_J[0] = jp;
     kk = 1;
     if (km <= 1) {
       __syncthreads();
@@ -298,13 +313,14 @@ struct Engine {
       int c0, c1;
       split(I.n, tm.size, tm.rank, c0, c1);
       for (int c = c0 + tid; c < c1; c += NT) {
-        if (c == jsel || ldcg(I.pos + c) >= 0) continue;
+        if (c == jp || ldcg(I.pos + c) >= 0) continue;
         const double wc = ldcg(I.w + c), uc = ldcg(I.u + c), an = ldcg(I.anorm + c);
-        if (uc > (100.0 * EPS) * an && wc >= thr_w && uc >= thr_u) {
+        const double wa = sgn ? fabs(wc) : wc;
+        if (uc > (100.0 * EPS) * an && wa >= thr_w && uc >= thr_u) {
           const int k = atomicAdd(&s_cnt, 1);
           if (k < CAND_LOCAL_MAX) {
-            s_k[k] = wkey(wc);
-            s_c[k] = c;
+            s_k[k] = wkey(wa);
+            s_c[k] = ext_of(c, wc);  // ties go to the lower index of [A -A]
           }
         }
       }
@@ -378,7 +394,7 @@ struct Engine {
     if (!sync()) return false;
     const int kc = s_kc;
     const int KK = kc + 1;
-    if (tid < KK) s_J[tid] = ldcg(I.J + tid);
+    if (tid < KK) s_J[tid] = phys(ldcg(I.J + tid));
     __syncthreads();
     if (KK == 1) return true;
     // (c) partial Gram matrix of the projected candidates over this CTA's rows
@@ -1044,8 +1060,10 @@ struct Engine {
   }
 
   // Feasibility loop of Algorithm 3: drop the last J column while
-  // min y_J <= 0 (and |J| > 1).  y_J only depends on the R22 triangle.
-  __device__ bool feasibility() {
+  // min y_J <= 0 (and |J| > 1).  y_J only depends on the R22 triangle.  With
+  // the positivity trick a J column enters with the sign of its w, and its y
+  // in [A -A] is that sign times the physical y.
+  __device__ bool feasibility(const int* s_J) {
     if (tm.rank == 0 && warp == 0) {
       __shared__ double s_y[KM];
       int k = kk, drops = 0;
@@ -1053,7 +1071,10 @@ struct Engine {
         solve_r22(k, s_y);
         __syncwarp();
         double mn = INFINITY;
-        for (int t = lane; t < k; t += 32) mn = fmin(mn, s_y[t]);
+        for (int t = lane; t < k; t += 32) {
+          const double sg = (sgn && ldcg(I.w + s_J[t]) < 0.0) ? -1.0 : 1.0;
+          mn = fmin(mn, sg * s_y[t]);
+        }
         mn = warp_max(-mn);
         mn = -mn;
         if (!(mn <= 0.0) || k <= 1) break;
@@ -2196,6 +2217,7 @@ struct Engine {
         I.pos[s_J[tid]] = nP + tid;
         I.xP[nP + tid] = 0.0;
         I.yP[nP + tid] = ldcg(I.yJ + tid);
+        if (sgn) I.csign[s_J[tid]] = ldcg(I.w + s_J[tid]) < 0.0 ? -1 : 1;
       }
     }
     // (b) trailing update of the Z columns and of Q^T b: D = V^T C (pass 1),
@@ -2286,10 +2308,36 @@ struct Engine {
     __shared__ double shv[32];
     __shared__ int shi[32];
     int steps = 0;
+    if (sgn == 2) {
+      // sign flip (section 4.2): a passive column whose y in [A -A] is
+      // negative gives way to its twin, whose R column is the negated one,
+      // so the physical R, y and W stay as they are and only the sign
+      // changes; the twin was in Z, so its previous iterate is 0.  Exact
+      // zeros of y are left to the ordinary inner step below.
+      __shared__ int s_nf;
+      if (tm.rank == 0) {
+        int nf = 0;
+        for (int p = tid; p < nP; p += NT) {
+          const int c = ldcg(I.order + p);
+          const int sc = ldcg(I.csign + c);
+          if ((double)sc * ldcg(I.yP + p) < 0.0) {
+            I.csign[c] = -sc;
+            I.xP[p] = 0.0;
+            ++nf;
+          }
+        }
+        nf = block_sum_int(nf, shi);
+        if (tid == 0) I.ctl[C_NFLIP] = nf;
+      }
+      if (!sync()) return false;
+      if (tid == 0) s_nf = ldcg(I.ctl + C_NFLIP);
+      __syncthreads();
+      n_flip += s_nf;
+    }
     for (;;) {
-      // any y_P <= 0 ?
+      // any y_P <= 0 ?  (with the positivity trick: y of the signed column)
       int neg = 0;
-      for (int p = tid; p < nP; p += NT) neg |= (ldcg(I.yP + p) <= 0.0);
+      for (int p = tid; p < nP; p += NT) neg |= (pos_sign(p) * ldcg(I.yP + p) <= 0.0);
       neg = block_sum_int(neg, shi);
       if (!neg) return true;
       if (steps > nP + 1) {
@@ -2301,13 +2349,15 @@ struct Engine {
       // alpha = min x_p/(x_p - y_p) over y_p <= 0; i* lowest column on ties
       ArgMax best{0.0, -1};
       for (int p = tid; p < nP; p += NT) {
-        const double yp = ldcg(I.yP + p);
-        if (yp <= 0.0) {
+        const double yp = ldcg(I.yP + p), sg = pos_sign(p);
+        if (sg * yp <= 0.0) {
+          // x/(x - y) is the same for the signed column (signs cancel)
           const double xp = ldcg(I.xP + p);
           const double t = xp / (xp - yp);
           const int c = ldcg(I.order + p);
           // minimise t: use (-t, c) in the argmax with lowest-index ties
-          best = amax_merge(best, ArgMax{-t, c});
+          // (the index in [A -A] with the positivity trick)
+          best = amax_merge(best, ArgMax{-t, sg < 0.0 ? c + I.n : c});
         }
       }
       best = block_amax(best, shv, shi);
@@ -2320,10 +2370,11 @@ struct Engine {
         if (tid == 0) s_nq = 0;
         __syncthreads();
         for (int p = tid; p < nP; p += NT) {
-          const double xp = ldcg(I.xP + p), yp = ldcg(I.yP + p);
+          const double xp = ldcg(I.xP + p), yp = ldcg(I.yP + p), sg = pos_sign(p);
           double xn = xp + alpha * (yp - xp);
-          if (ldcg(I.order + p) == istar) xn = 0.0;
-          if (xn <= 0.0) {
+          const int c = ldcg(I.order + p);
+          if ((sg < 0.0 ? c + I.n : c) == istar) xn = 0.0;
+          if (sg * xn <= 0.0) {
             xn = 0.0;
             const int k = atomicAdd(&s_nq, 1);
             qlist[k] = p;
@@ -2920,32 +2971,59 @@ struct Engine {
   // ------------------------------------------------------------ outputs
   __device__ bool finish() {
     __shared__ int shi[32];
-    // x and the sorted passive set
+    // x and the sorted passive set.  With the positivity trick x has 2n
+    // entries (x+, x-) and the passive set lists indices of [A -A]: every
+    // CTA counts its passive columns of either sign, so that the +1 columns
+    // come first (index j) and the -1 columns after them (index n + j).
     int c0, c1;
     split(I.n, tm.size, tm.rank, c0, c1);
-    int cnt = 0;
+    int cnt = 0, cneg = 0;
     for (int c = c0 + tid; c < c1; c += NT) {
       const int p = ldcg(I.pos + c);
-      I.x_out[c] = (p >= 0 && status != LHDM_ERR_NONFINITE) ? ldcg(I.xP + p) : 0.0;
-      cnt += (p >= 0);
+      const double v = (p >= 0 && status != LHDM_ERR_NONFINITE) ? ldcg(I.xP + p) : 0.0;
+      if (!sgn) {
+        I.x_out[c] = v;
+        cnt += (p >= 0);
+      } else {
+        const int sc = (p >= 0) ? ldcg(I.csign + c) : 0;
+        I.x_out[c] = sc > 0 ? v : 0.0;
+        I.x_out[I.n + c] = sc < 0 ? -v : 0.0;
+        cnt += (sc > 0);
+        cneg += (sc < 0);
+      }
     }
     cnt = block_sum_int(cnt, shi);
-    if (tid == 0) I.ipart[tm.rank * 8] = cnt;
-    if (!sync()) return false;
-    __shared__ int s_base;
+    cneg = block_sum_int(cneg, shi);
     if (tid == 0) {
-      int acc = 0;
-      for (int t = 0; t < tm.rank; ++t) acc += ldcg(I.ipart + t * 8);
+      I.ipart[tm.rank * 8] = cnt;
+      I.ipart[tm.rank * 8 + 1] = cneg;
+    }
+    if (!sync()) return false;
+    __shared__ int s_base, s_bneg;
+    if (tid == 0) {
+      int acc = 0, accn = 0, tot = 0;
+      for (int t = 0; t < tm.size; ++t) {
+        const int ct = ldcg(I.ipart + t * 8);
+        if (t < tm.rank) {
+          acc += ct;
+          accn += ldcg(I.ipart + t * 8 + 1);
+        }
+        tot += ct;
+      }
       s_base = acc;
+      s_bneg = tot + accn;
     }
     __syncthreads();
     if (tid == 0) {
-      int k = s_base;
-      for (int c = c0; c < c1; ++c)
-        if (ldcg(I.pos + c) >= 0) I.passive_out[k++] = c;
+      int k = s_base, kn = s_bneg;
+      for (int c = c0; c < c1; ++c) {
+        if (ldcg(I.pos + c) < 0) continue;
+        if (sgn && ldcg(I.csign + c) < 0) I.passive_out[kn++] = I.n + c;
+        else I.passive_out[k++] = c;
+      }
     }
     const int gt = tm.rank * NT + tid, nt = tm.size * NT;
-    for (int p = nP + gt; p < I.n; p += nt) I.passive_out[p] = -1;
+    for (int p = nP + gt; p < nx; p += nt) I.passive_out[p] = -1;
     if (tm.rank == 0 && tid == 0) {
       lhdm_info inf;
       inf.status = status;
@@ -2954,6 +3032,8 @@ struct Engine {
       inf.n_drop = n_drop;
       inf.n_passive = nP;
       inf.rank_limited = rank_limited;
+      inf.n_flip = n_flip;
+      inf.mode = sgn;
       inf.resid_norm = sqrt(rsq);
       inf.max_wZ = wz_any;
       inf.tol_w = tol_w;
@@ -2978,7 +3058,7 @@ struct Engine {
     if (!sync()) return fail_out();
     o1_reduce(true);
     tol_w = (I.prm.tol_w >= 0.0) ? I.prm.tol_w
-                                 : 10.0 * EPS * (double)max(I.m, I.n) * amax * sqrt(bsq);
+                                 : 10.0 * EPS * (double)max(I.m, nx) * amax * sqrt(bsq);
     if (nonfinite) {
       status = LHDM_ERR_NONFINITE;
       nP = 0;
@@ -2988,7 +3068,7 @@ struct Engine {
       return;
     }
     __shared__ int s_J[KM];
-    const int max_outer = I.prm.max_outer > 0 ? I.prm.max_outer : 3 * I.n;
+    const int max_outer = I.prm.max_outer > 0 ? I.prm.max_outer : 3 * nx;
     for (;;) {
       if (n_elig == 0 || !(wmax > tol_w)) {
         if (wz_any > tol_w) rank_limited = 1;
@@ -3015,7 +3095,7 @@ struct Engine {
         break;
       }
       phase(PH_FEAS);
-      if (!feasibility()) return fail_out();
+      if (!feasibility(s_J)) return fail_out();
       phase(PH_SOLVE);
       // y_P: rhs = (Q^T b)[0:nP] - R12 y_J, then back substitution
       {
@@ -3055,7 +3135,7 @@ struct Engine {
         tr[2] = inner_step;
         tr[3] = nP;
         tr[4] = removed;
-        tr[5] = s_J[0];
+        tr[5] = jsel;  // the first column of J (its index in [A -A] with the positivity trick)
       }
       o1_reduce(false);
       ++n_outer;
@@ -3074,6 +3154,8 @@ struct Engine {
       inf.n_drop = n_drop;
       inf.n_passive = nP;
       inf.rank_limited = rank_limited;
+      inf.n_flip = n_flip;
+      inf.mode = sgn;
       inf.resid_norm = -1.0;
       inf.max_wZ = 0.0;
       inf.tol_w = tol_w;

@@ -25,18 +25,21 @@ LHDM_ERR_ALLOC = 7
 LHDM_ERR_NO_STATE = 8
 LHDM_ERR_TOO_LARGE = 9
 KMAX_LIMIT = 64
+MODE_NNLS, MODE_SIGNED, MODE_SIGNED_FLIP = 0, 1, 2
 PHASES = ("setup", "dm", "panel", "solve", "commit", "inner", "residual", "dual",
           "feasibility", "chain", "zrot", "inner_trsv")
 
 
 class Params(C.Structure):
     _fields_ = [("tau1", C.c_double), ("tau2", C.c_double), ("delta", C.c_double),
-                ("tol_w", C.c_double), ("k_max", C.c_int32), ("max_outer", C.c_int32)]
+                ("tol_w", C.c_double), ("k_max", C.c_int32), ("max_outer", C.c_int32),
+                ("mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_outer", C.c_int32), ("n_inner", C.c_int32),
                 ("n_drop", C.c_int32), ("n_passive", C.c_int32), ("rank_limited", C.c_int32),
+                ("n_flip", C.c_int32), ("mode", C.c_int32),
                 ("resid_norm", C.c_double), ("max_wZ", C.c_double), ("tol_w", C.c_double)]
 
     def as_dict(self):
@@ -128,6 +131,11 @@ def _lda(A):
     return A.stride(1)
 
 
+def _nx(n, params):
+    """Length of x and of the passive list: n, or 2n in the signed modes."""
+    return 2 * n if (params is not None and params.mode != MODE_NNLS) else n
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -142,10 +150,11 @@ def solve_noalloc(A, b, params=None, x=None, passive=None, info=None, stream=Non
     m, n = A.shape
     lda = _lda(A)
     dev = A.device
+    nx = _nx(n, params)
     if x is None:
-        x = torch.empty(n, dtype=torch.float64, device=dev)
+        x = torch.empty(nx, dtype=torch.float64, device=dev)
     if passive is None:
-        passive = torch.empty(n, dtype=torch.int32, device=dev)
+        passive = torch.empty(nx, dtype=torch.int32, device=dev)
     if info is None:
         info = torch.zeros(C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
     rc = lib().lhdm_solve_noalloc(m, n, A.data_ptr() if A.numel() else None, lda,
@@ -193,10 +202,13 @@ class Context:
         lda = _lda(A)
         if b.dtype != torch.float64 or b.numel() != m or not b.is_contiguous():
             raise ValueError("b must be a contiguous float64 vector of length m")
+        nx = _nx(n, params)
         if x is None:
-            x = torch.empty(n, dtype=torch.float64, device=A.device)
+            x = torch.empty(nx, dtype=torch.float64, device=A.device)
         if passive is None:
-            passive = torch.empty(n, dtype=torch.int32, device=A.device)
+            passive = torch.empty(nx, dtype=torch.int32, device=A.device)
+        if x.numel() < nx or passive.numel() < nx:
+            raise ValueError("x and passive need %d entries" % nx)
         info = Info() if sync else None
         rc = lib().lhdm_solve(self.h, m, n, A.data_ptr(), lda, b.data_ptr(),
                               C.byref(params) if params is not None else None,
@@ -214,9 +226,9 @@ class Context:
         k = len(As)
         dev = As[0].device if k else torch.device("cuda")
         if xs is None:
-            xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A in As]
+            xs = [torch.empty(_nx(A.shape[1], params), dtype=torch.float64, device=dev) for A in As]
         if ps is None:
-            ps = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in As]
+            ps = [torch.empty(_nx(A.shape[1], params), dtype=torch.int32, device=dev) for A in As]
         if infos is None:
             infos = torch.zeros(max(k, 1) * C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
         m = _ints([A.shape[0] for A in As])
@@ -257,8 +269,8 @@ class Context:
         A = np.asfortranarray(A, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         m, n = A.shape
-        x = np.empty(n, dtype=np.float64)
-        p = np.empty(n, dtype=np.int32)
+        x = np.empty(_nx(n, params), dtype=np.float64)
+        p = np.empty(_nx(n, params), dtype=np.int32)
         info = Info()
         rc = lib().lhdm_solve_host(self.h, m, n, A.ctypes.data, max(1, m), b.ctypes.data,
                                    C.byref(params) if params is not None else None,
@@ -345,8 +357,8 @@ class Batch:
         k = len(As)
         self.k = k
         dev = As[0].device if k else torch.device("cuda")
-        self.xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A in As]
-        self.ps = [torch.empty(A.shape[1], dtype=torch.int32, device=dev) for A in As]
+        self.xs = [torch.empty(_nx(A.shape[1], params), dtype=torch.float64, device=dev) for A in As]
+        self.ps = [torch.empty(_nx(A.shape[1], params), dtype=torch.int32, device=dev) for A in As]
         self.infos = torch.zeros(max(k, 1) * C.sizeof(Info) // 8, dtype=torch.float64, device=dev)
         m = (C.c_int32 * max(k, 1))(*[A.shape[0] for A in As])
         n = (C.c_int32 * max(k, 1))(*[A.shape[1] for A in As])
