@@ -106,6 +106,27 @@ def nnls_signed(A, b, sign_flip=False, **kw):
     return nnls(A2, b, twin_n=A.shape[1], sign_flip=sign_flip, **kw)
 
 
+def l1_stack(A, b, lam):
+    """The l1-NNLS system of section 3.3, eq. (l1_NNLS), written out: the
+    (m+1) x 2n matrix [1^T 1^T; lam A  -lam A] and the right-hand side
+    [0; lam b] (column-major)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    M = np.empty((m + 1, 2 * n))
+    M[0, :] = 1.0
+    M[1:, :n] = lam * A
+    M[1:, n:] = -lam * A
+    rhs = np.concatenate([[0.0], lam * np.asarray(b, dtype=np.float64)])
+    return np.asfortranarray(M), rhs
+
+
+def nnls_l1(A, b, lam, **kw):
+    """l1-NNLS (section 3.3): NNLS on l1_stack(A, b, lam); x = (x+, x-) of
+    length 2n.  Returns the dict of nnls()."""
+    M, rhs = l1_stack(A, b, lam)
+    return nnls(M, rhs, **kw)
+
+
 def dm_select(C_, w, u, tau1, tau2, delta, k_max):
     """Algorithm 2 on an explicit candidate matrix; returns the ordered J."""
     C_ = np.asfortranarray(C_, dtype=np.float64)

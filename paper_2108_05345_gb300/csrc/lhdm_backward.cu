@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(NT, 1) lhdm_backward_batch_kernel(const BatchI
   extern __shared__ double dyn[];
   __shared__ int s_k;
   Inst I;
+  I.prm = DevParams{};  // plain NNLS: the adjoint reads no solver parameter
   const size_t dbase = (size_t)blockIdx.x * L.dtotal;
   bind_scratch(I, L, dscr + dbase, iscr + (size_t)blockIdx.x * L.itotal);
   I.phase_ns = nullptr;

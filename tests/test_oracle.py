@@ -492,3 +492,61 @@ def test_positivity_trick_brute_force():
         for flip in (False, True):
             r = O.nnls_signed(A, b, sign_flip=flip, k_max=4)
             assert abs(r["resid_norm"] - res_bf) <= 1e-10 * max(1.0, np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------- l1-NNLS
+def l1_subgradient_gap(A, b, lam, xs):
+    """Optimality of x = x+ - x- for f(x) = ||x||_1^2 + lam^2 ||A x - b||^2
+    (the objective of eq. (l1_NNLS) once x+ * x- = 0): with
+    g = lam^2 A^T (b - A x) and t = ||x||_1, 0 is in the subdifferential
+    iff g_i = t sign(x_i) where x_i != 0 and |g_i| <= t where x_i = 0.
+    Returns the largest violation relative to t."""
+    g = lam * lam * (A.T @ (b - A @ xs))
+    t = np.abs(xs).sum()
+    nz = xs != 0
+    v1 = np.abs(g[nz] - t * np.sign(xs[nz])).max() if nz.any() else 0.0
+    v2 = max(0.0, (np.abs(g[~nz]) - t).max()) if (~nz).any() else 0.0
+    return max(v1, v2) / max(t, 1e-300)
+
+
+@pytest.mark.parametrize("lam", [0.5, 3.0, 30.0])
+def test_l1_nnls_optimality(lam):
+    """The oracle's l1-NNLS solution, with x = x+ - x-, minimises
+    ||x||_1^2 + lam^2 ||A x - b||^2: the subgradient condition holds, the two
+    halves never overlap, and the stacked residual equals the objective."""
+    for seed in range(3):
+        A, b, _ = WL.signed_recovery(seed, m=60, n=120, s=8)
+        for k in (1, 8):
+            r = O.nnls_l1(A, b, lam, k_max=k)
+            assert r["status"] == O.OK
+            n = A.shape[1]
+            xp, xm = r["x"][:n], r["x"][n:]
+            assert not (xp * xm).any()
+            xs = xp - xm
+            assert l1_subgradient_gap(A, b, lam, xs) <= 1e-9
+            f = np.abs(xs).sum() ** 2 + lam * lam * np.sum((A @ xs - b) ** 2)
+            assert abs(r["resid_norm"] ** 2 - f) <= 1e-10 * max(1.0, f)
+
+
+def test_l1_nnls_single_column_closed_form():
+    """n = 1: min x^2 + lam^2 ||a x - b||^2 gives x = lam^2 a^T b / (1 + lam^2 ||a||^2)."""
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        a = rng.normal(size=(9, 1))
+        b = rng.normal(size=9)
+        lam = rng.uniform(0.2, 5.0)
+        r = O.nnls_l1(a, b, lam, k_max=2)
+        xs = r["x"][0] - r["x"][1]
+        expect = lam ** 2 * float(a[:, 0] @ b) / (1.0 + lam ** 2 * float(a[:, 0] @ a[:, 0]))
+        assert abs(xs - expect) <= 1e-14 * max(1.0, abs(expect))
+
+
+def test_l1_nnls_brute_force():
+    """Tiny cases: the oracle's optimum equals brute-force enumeration on the
+    explicit stacked matrix (5 x 8)."""
+    for seed in range(8):
+        A, b = WL.tiny(seed, 4, 4)
+        M, rhs = O.l1_stack(A, b, 2.0)
+        res_bf, _, _ = brute_force_nnls(M, rhs)
+        r = O.nnls_l1(A, b, 2.0, k_max=4)
+        assert abs(r["resid_norm"] - res_bf) <= 1e-10 * max(1.0, np.linalg.norm(rhs))
