@@ -267,6 +267,29 @@ int lhdm_backward_batched(lhdm_ctx* ctx, const double* const* dLdx, double* cons
                           double* const* dLdA, const int32_t* ld_dA, void* stream);
 
 /*
+ * lhdm_solve_l1: l1-NNLS (section 3.3, eq. (l1_NNLS)), the squared-l1
+ * regularised least squares  min ||x||_1^2 + lambda^2 ||A x - b||^2  recast
+ * as NNLS on the (m+1) x 2n system
+ *     [1^T  1^T; lambda A  -lambda A] (x+; x-) = (0; lambda b),  x+, x- >= 0.
+ * The stacked system is written into a buffer of the context by one kernel
+ * (one read of A, two column writes) and solved by lhdm_solve.
+ *  m, n, A, lda, b  the data of the regularised problem (A device, m x n,
+ *                 column-major; b device, length m); the context must allow
+ *                 m + 1 rows and 2n columns (max_m >= m+1, max_n >= 2n).
+ *  lambda         > 0, the weight of the residual.
+ *  prm            host, NULL = defaults; prm->mode must be LHDM_MODE_NNLS.
+ *  x, passive     device, 2n entries: (x+, x-) and the passive set of the
+ *                 stacked system (indices j < n for x+_j, n + j for x-_j).
+ *  info           host or NULL, as lhdm_solve.
+ * The first call on a context allocates the stacked buffers (about
+ * 8 * max_m * max_n bytes); later calls allocate nothing.  No adjoint state
+ * is kept.  Errors: INVALID_ARG, ALLOC, CUDA.
+ */
+int lhdm_solve_l1(lhdm_ctx* ctx, int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
+                  double lambda, const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info,
+                  void* stream);
+
+/*
  * Bound, in nanoseconds, on every wait of one CTA for another in the solves
  * and adjoints launched on ctx after this call (the grid barrier, the flags
  * of the pipelined triangular solve and of the rotation log); ns <= 0

@@ -58,6 +58,9 @@ struct lhdm_ctx {
   lhdm_params pprm{};
   bool batch_state = false;
   int* d_zero = nullptr;  // one int 0: the work-queue order of a one-instance adjoint
+  // l1-NNLS: the stacked system (allocated by the first lhdm_solve_l1)
+  double* l1A = nullptr;  // max_m x max_n, ld = L.ldw
+  double* l1b = nullptr;  // max_m
 };
 
 struct lhdm_batch {
@@ -230,6 +233,8 @@ int lhdm_destroy(lhdm_ctx* c) {
   cudaFree(c->hx);
   cudaFree(c->hp);
   cudaFree(c->d_zero);
+  cudaFree(c->l1A);
+  cudaFree(c->l1b);
   if (c->plan) lhdm_batch_destroy(c->plan);
   delete c;
   return LHDM_OK;
@@ -429,6 +434,52 @@ int lhdm_backward(lhdm_ctx* c, int32_t idx, const double* A, int32_t lda, const 
                   (void*)&dLdA, (void*)&ld_dA, (void*)&apu_arg};
   e = cudaLaunchCooperativeKernel((const void*)lhdm_backward_grid_kernel, dim3(c->nsm), dim3(NT), args, DYN_SMEM, st);
   return cuda_ok(e);
+}
+
+// ----------------------------------------------------------------------- l1-NNLS
+// The system of eq. (l1_NNLS): column j of [1^T 1^T; lam A  -lam A] for j < n
+// and its partner n + j, from column j of A (one read of A, two writes);
+// the right-hand side [0; lam b] by the first column block.
+__global__ void lhdm_l1_stack_kernel(int m, int n, const double* __restrict__ A, int lda,
+                                     const double* __restrict__ b, double lam, double* __restrict__ S, int lds,
+                                     double* __restrict__ rhs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // row of the stacked system
+  if (i > m) return;
+  for (int j = blockIdx.y; j < n; j += gridDim.y) {
+    const double v = (i == 0) ? 0.0 : lam * A[(size_t)j * lda + i - 1];
+    S[(size_t)j * lds + i] = (i == 0) ? 1.0 : v;
+    S[(size_t)(n + j) * lds + i] = (i == 0) ? 1.0 : -v;
+  }
+  if (blockIdx.y == 0) rhs[i] = (i == 0) ? 0.0 : lam * b[i - 1];
+}
+
+int lhdm_solve_l1(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, const double* b, double lambda,
+                  const lhdm_params* prm, double* x, int32_t* passive, lhdm_info* info, void* stream) {
+  if (!c || m < 0 || n < 0 || m + 1 > c->max_m || 2 * (int64_t)n > c->max_n || lda < std::max(1, m))
+    return LHDM_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && !A) || (m > 0 && !b) || (n > 0 && (!x || !passive))) return LHDM_ERR_INVALID_ARG;
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return LHDM_ERR_INVALID_ARG;
+  if (prm && prm->mode != LHDM_MODE_NNLS) return LHDM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->l1A) {
+    e = cudaMalloc(&c->l1A, (size_t)c->L.ldw * std::max(c->max_n, 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->l1b, (size_t)std::max(c->max_m, 1) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(c->l1A);
+      cudaFree(c->l1b);
+      c->l1A = nullptr;
+      c->l1b = nullptr;
+      return LHDM_ERR_ALLOC;
+    }
+  }
+  const int ld = c->L.ldw;
+  const dim3 grid((unsigned)((m + 1 + 255) / 256), (unsigned)std::max(1, std::min(n, 65535)));
+  lhdm_l1_stack_kernel<<<grid, 256, 0, st>>>(m, n, A, lda, b, lambda, c->l1A, ld, c->l1b);
+  if (cudaGetLastError() != cudaSuccess) return LHDM_ERR_CUDA;
+  const int rc = lhdm_solve(c, m + 1, 2 * n, c->l1A, ld, c->l1b, prm, x, passive, info, stream);
+  c->have_state = false;  // the adjoint of lhdm_backward is for the caller's own A
+  return rc;
 }
 
 int lhdm_set_wait_limit(lhdm_ctx* c, int64_t ns) {

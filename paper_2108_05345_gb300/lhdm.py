@@ -74,6 +74,7 @@ def lib():
         L.lhdm_get_info.argtypes = [V, I, V]
         L.lhdm_backward.argtypes = [V, i32, d, i32, d, d, d, i32, V]
         L.lhdm_set_wait_limit.argtypes = [V, C.c_int64]
+        L.lhdm_solve_l1.argtypes = [V, i32, i32, d, i32, d, C.c_double, P, d, d, I, V]
         L.lhdm_debug_stall_next_solve.argtypes = [V]
         L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
         L.lhdm_trace.argtypes = [V, C.POINTER(C.c_int32), i32, V]
@@ -304,6 +305,30 @@ class Context:
                                  dA.data_ptr() if dA is not None else None, max(1, m), _stream(stream))
         _check(rc, "lhdm_backward")
         return db, dA
+
+    def solve_l1(self, A, b, lam, params=None, x=None, passive=None, stream=None, sync=True):
+        """lhdm_solve_l1: l1-NNLS (section 3.3) with weight lam; returns
+        (x of length 2n = (x+, x-), passive of the stacked system, info)."""
+        m, n = A.shape
+        lda = _lda(A)
+        if b.dtype != torch.float64 or b.numel() != m or not b.is_contiguous():
+            raise ValueError("b must be a contiguous float64 vector of length m")
+        if x is None:
+            x = torch.empty(2 * n, dtype=torch.float64, device=A.device)
+        if passive is None:
+            passive = torch.empty(2 * n, dtype=torch.int32, device=A.device)
+        info = Info() if sync else None
+        rc = lib().lhdm_solve_l1(self.h, m, n, A.data_ptr(), lda, b.data_ptr(), float(lam),
+                                 C.byref(params) if params is not None else None,
+                                 x.data_ptr(), passive.data_ptr(),
+                                 C.byref(info) if info is not None else None, _stream(stream))
+        _check(rc, "lhdm_solve_l1")
+        return x, passive, (info.as_dict() if info is not None else None)
+
+    def l1_path(self, A, b, lams, params=None):
+        """l1-NNLS for each weight of a sweep; returns a list of (x, passive, info)."""
+        return [tuple(t.clone() if torch.is_tensor(t) else t for t in self.solve_l1(A, b, lam, params))
+                for lam in lams]
 
     def set_wait_limit(self, ns):
         _check(lib().lhdm_set_wait_limit(self.h, int(ns)), "lhdm_set_wait_limit")
