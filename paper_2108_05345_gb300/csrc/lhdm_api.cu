@@ -49,6 +49,7 @@ struct lhdm_ctx {
   // bounded waits (0 = default) and the failure-detection test's stall
   long long wait_ns = 0;
   bool stall_next = false;
+  int guard_force = 0;  // test aid for the tensor-core commit's accuracy guard
   // batched solves: the plan of the last lhdm_solve_batched and the
   // arguments it was made for (reused while they repeat)
   int max_batch = 0;
@@ -255,6 +256,7 @@ static void fill_ctx_inst(lhdm_ctx* c, Inst& I) {
   I.trace = c->d_trace;
   I.trace_cap = c->trace_cap;
   I.wait_ns = c->wait_ns > 0 ? c->wait_ns : WAIT_NS;
+  I.guard_force = c->guard_force;
 }
 
 int lhdm_solve(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t lda, const double* b,
@@ -377,6 +379,7 @@ int lhdm_debug_state(lhdm_ctx* c, const char* name, void* host, int64_t count, v
       {"r", c->r, 8, m},                      {"W", c->dscr + c->L.W, 8, (size_t)c->L.ldw * n},
       {"R", c->R, 8, (size_t)c->ldr * cp},    {"order", c->order, 4, cp},
       {"rslot", c->rslot, 4, cp},             {"pos", c->iscr + c->L.pos, 4, n},
+      {"ctl", c->iscr + c->L.ctl, 4, 16},
   };
   for (const Entry& e : table) {
     if (std::strcmp(e.nm, name) != 0) continue;
@@ -485,6 +488,12 @@ int lhdm_solve_l1(lhdm_ctx* c, int32_t m, int32_t n, const double* A, int32_t ld
 int lhdm_set_wait_limit(lhdm_ctx* c, int64_t ns) {
   if (!c) return LHDM_ERR_INVALID_ARG;
   c->wait_ns = ns > 0 ? (long long)ns : 0;
+  return LHDM_OK;
+}
+
+int lhdm_debug_commit_guard(lhdm_ctx* c, int32_t mode) {
+  if (!c || mode < 0 || mode > 2) return LHDM_ERR_INVALID_ARG;
+  c->guard_force = mode;
   return LHDM_OK;
 }
 

@@ -128,11 +128,15 @@ struct Inst {
   long long wait_ns;          // bound on a wait for another CTA (ns)
   int bar_extra;              // failure-detection test: arrivals the grid barrier
                               // expects beyond the grid (0 in every normal solve)
+  int guard_force;            // test aid: 1 sends every tensor-core commit batch to
+                              // FP64, 2 every pass-2 element (0 in normal solves)
   DevParams prm;
 };
 
 // control words (ctl[])
-enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK, C_NFLIP };
+enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK, C_NFLIP,
+       C_GUARD1,   // commit batches the accuracy guard handed to the FP64 path
+       C_GUARD2 }; // commit elements it recomputed in FP64
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }

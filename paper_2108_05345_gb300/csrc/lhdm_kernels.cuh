@@ -136,6 +136,7 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.amask = nullptr;
   I.wait_ns = WAIT_NS;
   I.bar_extra = 0;
+  I.guard_force = 0;
 }
 
 inline __device__ void bind_item(Inst& I, const BatchItem& it) {

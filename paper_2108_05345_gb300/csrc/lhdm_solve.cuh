@@ -12,6 +12,20 @@ constexpr int CAND_LOCAL_MAX = 2048;     // local DM candidates per CTA
 constexpr int CAND_STAGE = 4096;         // merged candidates staged per pass
 constexpr int ROT_STAGE = 2048;          // rotations staged per pass
 
+// One element of the tensor-core commit's pass 2 in FP64 (its accuracy
+// guard's fallback): x - sum_t V(row, t) E(t), in the order of the FP64
+// commit, with V row-major (ld KM, reflector t zero above row t and v0 on
+// row t) and E = column c of D' (stride CB).  Out of line: it is rare.
+__device__ __noinline__ double commit_elem_fp64(const double* V, const double* vtop, const double* E, int kp, int row,
+                                                double x, int* counter) {
+  for (int t = 0; t < kp; ++t) {
+    const double vt = (row > t) ? __ldcg(V + (size_t)row * KM + t) : ((row == t) ? vtop[t] : 0.0);
+    x = fma(-vt, E[t * 16], x);
+  }
+  atomicAdd(counter, 1);
+  return x;
+}
+
 // Orderable key of a positive double (dual values of DM candidates are > 0).
 __device__ __forceinline__ unsigned long long wkey(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -1765,8 +1779,25 @@ struct Engine {
   // side, 16-byte chunks XOR-swizzled by row so that ldmatrix is
   // conflict-free), pass-1 C' digit buffers in the upper halves of those
   // (pass 1 has R = 64), D' digits at 128K.
+  // Accuracy guard of the digit products.  The fixed-point digits carry 56
+  // bits under one power-of-two scale per V row and per column of C' (pass 1)
+  // or D' (pass 2), so a sum whose terms are all far below the scale loses
+  // bits that an FP64 dot product would keep.  Each pass therefore also forms
+  // the sum of |leading digit| products (one more MMA per step, exact
+  // integers): a lower bound of sum |v||c| in units of 2^(scale - 14).  The
+  // digit result's error is at most 2L 2^(Ec-57) in pass 1 and
+  // (3k+2) 2^(Er+Ee-57) in pass 2; where that could exceed the worst-case
+  // bound of the FP64 evaluation, gamma_L sum |v||c| (pass 1) or
+  // gamma_(k+1) (|x| + sum |v||e|) (pass 2), the FP64 path takes over: the
+  // whole batch (pass 1, before C is touched) or the single element (pass 2).
+  static constexpr float GUARD1 = 2048.0f;  // 2^11: sum |v||c| >= 2^(Ec-3)
+  static constexpr double GUARD2 = 3072.0;  // 3 * 2^10: |x| + sum |v||e| >= 3 * 2^(Er+Ee-4)
+  static constexpr unsigned ABS2 = 0x7FFF7FFFu;  // clears the signs of a bf16 pair
+
+  // Returns 0 when the batch is committed, 1 when a bounded wait expired, 2
+  // when the accuracy guard hands the batch to the FP64 path (C untouched).
   template <int NBP, int KT>
-  __device__ bool commit_tc(const CommitShape& cs, int nb) {
+  __device__ int commit_tc(const CommitShape& cs, int nb) {
     constexpr int NTN = NBP / 8;           // column tiles
     constexpr int COMBOS = KT * NTN;       // (reflector tile, column tile) pairs
     constexpr int MW = COMBOS * 4;         // pass-1 MMA warps
@@ -1905,6 +1936,7 @@ struct Engine {
     for (int l = 0; l < NLV; ++l)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[l][j] = 0.f;
+    float gacc[4] = {0.f, 0.f, 0.f, 0.f};  // sum of |leading digit| products (guard)
     int since = 0;
     // every CTA walks the chunks from its own starting chunk, so that the
     // CTAs do not all ask for the same digit rows at the same moment (the
@@ -1921,7 +1953,7 @@ struct Engine {
       const bool okv = wait_v(b);
       if (__syncthreads_or(!okv)) {
         expired();
-        return false;
+        return 1;
       }
       if (jc + 1 < nch1) {
         stage_c(row1(jc + 1), b ^ 1);
@@ -1941,6 +1973,11 @@ struct Engine {
           ldsm_x4_t(a, vaddr(sAb, R1, k, ra, qa));
 #pragma unroll
           for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(acc[k + l], a, bq[l]);
+          if (k == 0) {
+            const unsigned ga[4] = {a[0] & ABS2, a[1] & ABS2, a[2] & ABS2, a[3] & ABS2};
+            const unsigned gb[2] = {bq[0][0] & ABS2, bq[0][1] & ABS2};
+            mma_bf16(gacc, ga, gb);
+          }
         }
       }
       if (jc + 1 < nch1) {
@@ -1963,15 +2000,36 @@ struct Engine {
     // levels NEX .. 8 summed over the sub-blocks in order, then D from the
     // level sums
     __syncthreads();
-    float* sStage = reinterpret_cast<float*>(sV);                                 // MW x (NLV-NEX) x 32 x 4
+    constexpr int NST = NLV - NEX + 1;  // staged FP32 sums per warp: levels NEX .. 8 and the guard
+    float* sStage = reinterpret_cast<float*>(sV);                                 // MW x NST x 32 x 4
     double* sL = reinterpret_cast<double*>(reinterpret_cast<char*>(sV) + 73728);  // NLV x 32 x NBP
+    __shared__ int s_guard;
+    if (tid == 0) s_guard = 0;
     if (mw) {
 #pragma unroll
       for (int l = NEX; l < NLV; ++l)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sStage[((warp * (NLV - NEX) + l - NEX) * 32 + lane) * 4 + j] = acc[l][j];
+        for (int j = 0; j < 4; ++j) sStage[((warp * NST + l - NEX) * 32 + lane) * 4 + j] = acc[l][j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sStage[((warp * NST + NST - 1) * 32 + lane) * 4 + j] = gacc[j];
     }
     __syncthreads();
+    // guard of pass 1: every (reflector, column) sum of |leading digit|
+    // products over the four row sub-blocks must reach GUARD1
+    for (int e = tid; e < COMBOS * 128; e += NT) {
+      const int j = e & 3, ln = (e >> 2) & 31, cb = e >> 7;
+      const int t = (cb % KT) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb / KT) * 8 + 2 * (ln & 3) + (j & 1);
+      if (t < kp && c < nb) {
+        float g = 0.f;
+        for (int sb = 0; sb < 4; ++sb) g += sStage[(((sb * COMBOS + cb) * NST + NST - 1) * 32 + ln) * 4 + j];
+        if (!(g >= GUARD1)) s_guard = 1;
+      }
+    }
+    __syncthreads();
+    if (s_guard || I.guard_force == 1) {
+      if (tid == 0) atomicAdd(I.ctl + C_GUARD1, 1);
+      return 2;
+    }
     for (int e = tid; e < COMBOS * NLV * 128; e += NT) {
       const int j = e & 3, ln = (e >> 2) & 31, lam = (e >> 7) % NLV, cb = (e >> 7) / NLV;
       double v = 0.0;
@@ -1979,7 +2037,7 @@ struct Engine {
         v = (double)sF[((cb * NEX + lam) * 32 + ln) * 4 + j];
       } else {
         for (int sb = 0; sb < 4; ++sb)
-          v += (double)sStage[(((sb * COMBOS + cb) * (NLV - NEX) + lam - NEX) * 32 + ln) * 4 + j];
+          v += (double)sStage[(((sb * COMBOS + cb) * NST + lam - NEX) * 32 + ln) * 4 + j];
       }
       const int t = (cb % KT) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb / KT) * 8 + 2 * (ln & 3) + (j & 1);
       sL[(lam * 32 + t) * NBP + c] = v;
@@ -2034,7 +2092,7 @@ struct Engine {
       const bool okv = wait_v(b);
       if (__syncthreads_or(!okv)) {
         expired();
-        return false;
+        return 1;
       }
       if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
@@ -2052,6 +2110,7 @@ struct Engine {
         for (int l = 0; l < NLV; ++l)
 #pragma unroll
           for (int j = 0; j < 4; ++j) a2[l][j] = 0.f;
+        float g2[4] = {0.f, 0.f, 0.f, 0.f};  // sum of |leading digit| products (guard)
         const unsigned short* sAb = sV + b * BUF;
         const int r0 = rt * 16, rq = r0 + (lane & 7) + ((lane >> 3) & 1) * 8;
 #pragma unroll
@@ -2066,6 +2125,11 @@ struct Engine {
             ldsm_x4(a, vaddr(sAb, R2, k, rq, ks * 2 + ((lane >> 4) & 1)));
 #pragma unroll
             for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(a2[k + l], a, eb[l]);
+            if (k == 0) {
+              const unsigned ga[4] = {a[0] & ABS2, a[1] & ABS2, a[2] & ABS2, a[3] & ABS2};
+              const unsigned gb[2] = {eb[0][0] & ABS2, eb[0][1] & ABS2};
+              mma_bf16(g2, ga, gb);
+            }
           }
         }
 #pragma unroll
@@ -2079,8 +2143,14 @@ struct Engine {
             for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
-            const int es = max(-2044, ((j < 2) ? er0 : er1) + s_Ee[c] - 57);
-            const double x = xv[j] - scale2((double)u, es);
+            const int esc = ((j < 2) ? er0 : er1) + s_Ee[c];  // exponent of the product scale
+            const int es = max(-2044, esc - 57);
+            double x = xv[j] - scale2((double)u, es);
+            // guard of pass 2: 2^14 |x| / 2^(Er+Ee) + sum |leading digit
+            // products| below GUARD2 -> this element in FP64, in the order of
+            // the FP64 commit
+            if (I.guard_force == 2 || !((double)g2[j] + scale2(fabs(xv[j]), max(-2044, min(2044, 14 - esc))) >= GUARD2))
+              x = commit_elem_fp64(I.V, cs.s_vt, cs.s_E + c, kp, row, xv[j], I.ctl + C_GUARD2);
             p[row] = x;
             if (row >= kp) {
               if (j & 1) nrm1 = fma(x, x, nrm1);
@@ -2106,7 +2176,7 @@ struct Engine {
       for (int r8 = 0; r8 < 8; ++r8) v += cs.s_nrm[r8 * CB + tid];
       if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
     }
-    return true;
+    return 0;
   }
 
 
@@ -2270,11 +2340,12 @@ struct Engine {
       __syncthreads();
       if constexpr (std::is_same<Team, GridTeam>::value) {  // only whole-grid teams have digits
         if (tc) {
-          bool ok;
-          if (kp <= 16) ok = (nb <= 8) ? commit_tc<8, 1>(cs, nb) : commit_tc<16, 1>(cs, nb);
-          else ok = (nb <= 8) ? commit_tc<8, 2>(cs, nb) : commit_tc<16, 2>(cs, nb);
-          if (!ok) return false;
-          continue;
+          int r;
+          if (kp <= 16) r = (nb <= 8) ? commit_tc<8, 1>(cs, nb) : commit_tc<16, 1>(cs, nb);
+          else r = (nb <= 8) ? commit_tc<8, 2>(cs, nb) : commit_tc<16, 2>(cs, nb);
+          if (r == 1) return false;
+          if (r == 0) continue;
+          __syncthreads();  // r == 2: the FP64 commit below takes this batch
         }
       }
       switch (nb) {

@@ -76,6 +76,7 @@ def lib():
         L.lhdm_set_wait_limit.argtypes = [V, C.c_int64]
         L.lhdm_solve_l1.argtypes = [V, i32, i32, d, i32, d, C.c_double, P, d, d, I, V]
         L.lhdm_debug_stall_next_solve.argtypes = [V]
+        L.lhdm_debug_commit_guard.argtypes = [V, i32]
         L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
         L.lhdm_trace.argtypes = [V, C.POINTER(C.c_int32), i32, V]
         L.lhdm_debug_state.argtypes = [V, C.c_char_p, C.c_void_p, C.c_int64, V]
@@ -333,6 +334,9 @@ class Context:
     def set_wait_limit(self, ns):
         _check(lib().lhdm_set_wait_limit(self.h, int(ns)), "lhdm_set_wait_limit")
 
+    def force_commit_guard(self, mode):
+        _check(lib().lhdm_debug_commit_guard(self.h, int(mode)), "lhdm_debug_commit_guard")
+
     def stall_next_solve(self):
         _check(lib().lhdm_debug_stall_next_solve(self.h), "lhdm_debug_stall_next_solve")
 
@@ -350,7 +354,7 @@ class Context:
     def state(self, name, count, stream=None):
         """lhdm_debug_state: a named piece of the solver state as numpy."""
         import numpy as np
-        dt = np.int32 if name in ("order", "rslot", "pos") else np.float64
+        dt = np.int32 if name in ("order", "rslot", "pos", "ctl") else np.float64
         out = np.empty(int(count), dtype=dt)
         _check(lib().lhdm_debug_state(self.h, name.encode(), out.ctypes.data, int(count), _stream(stream)),
                "lhdm_debug_state")

@@ -6,9 +6,18 @@ a value x with |x| < 2^E is Y = round(|x| 2^(56-E)), cut into eight 7-bit
 digits; V rows carry a row scale 2^Er, C' = 2^Er C and E carry column
 scales; products of digits are summed per level k + l <= 8 exactly, and the
 levels are recombined (pass 2 in int64 with levels 7 and 8 rounded down).
-This test restates those steps in Python integers and checks that the
-result is as close to the exact (rational) product as an FP64 evaluation,
-on operands whose rows span 2^-20 .. 2^20.
+This test restates those steps in Python integers (with the FP32 and int32
+accumulation of the level sums as the kernel does it: 16-row MMA steps,
+levels 0-6 moved into int32 every 128 rows, levels 7-8 kept in FP32) and
+checks the result against the exact (rational) product.
+
+The fixed point is accurate relative to the column scale, not to each
+term: where every term of a sum lies far below the scale (a large entry of
+C paired with a zero of V, say), the digits lose bits an FP64 dot product
+keeps.  The kernel's accuracy guard (sum of |leading digit| products, one
+more MMA) detects that and hands the batch (pass 1) or the element (pass 2)
+to FP64; with the guard the result is within the worst-case bound of the
+FP64 evaluation, gamma_L sum |v||c|, element by element.
 """
 import math
 import struct
@@ -57,24 +66,92 @@ def levels(a, b):
     return lev
 
 
-def commit_digits(V, C, T, kp):
+NEX = 7  # levels moved into int32 sums every 128 rows
+
+
+def levels_pass1(a, b):
+    """Pass-1 level sums as the kernel accumulates them: 16-row MMA steps
+    summed in FP32 (exact below 2^24); every 128 rows levels 0 .. NEX-1 are
+    moved into int32 (checked for overflow) and restart, levels NEX .. 8 keep
+    accumulating in FP32 (rounded)."""
+    L = len(a)
+    lev_int = [0] * NEX
+    lev_f = [np.float32(0.0)] * (ND + 1 - NEX)
+    blk = [np.float32(0.0)] * NEX
+    for r0 in range(0, L, 16):
+        step = levels(a[r0:r0 + 16], b[r0:r0 + 16])
+        for lam in range(NEX):
+            v = np.float32(blk[lam]) + np.float32(step[lam])
+            assert abs(float(v)) < 2 ** 24 and float(v) == float(blk[lam]) + step[lam]  # exact in FP32
+            blk[lam] = v
+        for lam in range(NEX, ND + 1):
+            lev_f[lam - NEX] = np.float32(lev_f[lam - NEX] + np.float32(step[lam]))
+        if (r0 // 16) % 8 == 7 or r0 + 16 >= L:
+            for lam in range(NEX):
+                lev_int[lam] += int(blk[lam])
+                assert abs(lev_int[lam]) < 2 ** 31
+                blk[lam] = np.float32(0.0)
+    return lev_int + [float(v) for v in lev_f]
+
+
+def guard_pass1(a, bC, kp, nb):
+    """Sum of |leading digit| products per (reflector, column): the pass-1
+    accuracy guard's quantity (the batch goes to FP64 below 2^11)."""
+    L = len(a)
+    return np.array([[sum(abs(a[r][t][0]) * abs(bC[r][c][0]) for r in range(L)) for c in range(nb)]
+                     for t in range(kp)], dtype=float)
+
+
+def commit_digits(V, C, T, kp, guard=False):
+    """The tensor-core commit restated; with guard=True its accuracy guard
+    too (FP64 for the whole batch when pass 1's guard fires, for an element
+    when pass 2's does).  Returns D, E, the updated C and the guard counts."""
     L, nb = V.shape[0], C.shape[1]
     Er = [max(ebound(v) for v in V[r, :kp]) for r in range(L)]
     a = [[digits(V[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
     Ec = [max([ebound(C[r, c]) + Er[r] for r in range(L) if ebound(C[r, c]) > -2000] or [-8000]) for c in range(nb)]
     bC = [[digits(C[r, c], Er[r] + 56 - Ec[c]) for c in range(nb)] for r in range(L)]
+    if guard and (guard_pass1(a, bC, kp, nb) < 2048).any():
+        D = np.zeros((kp, nb))
+        for t in range(kp):
+            for c in range(nb):
+                acc = 0.0
+                for r in range(L):
+                    acc = acc + V[r, t] * C[r, c]
+                D[t, c] = acc
+        E = T[:kp, :kp].T @ D
+        Cn = C.copy()
+        for r in range(L):
+            for c in range(nb):
+                x = C[r, c]
+                for t in range(kp):
+                    x = x - V[r, t] * E[t, c]
+                Cn[r, c] = x
+        return D, E, Cn, (1, 0)
     D = np.zeros((kp, nb))
     for t in range(kp):
         for c in range(nb):
-            lev = levels([a[r][t] for r in range(L)], [bC[r][c] for r in range(L)])
+            lev = levels_pass1([a[r][t] for r in range(L)], [bC[r][c] for r in range(L)])
             s = float(lev[ND])
             for lam in range(ND - 1, -1, -1):
                 s = s * 2.0 ** -7 + lev[lam]
             D[t, c] = math.ldexp(s, Ec[c] - 14)
     E = T[:kp, :kp].T @ D
+    Cn, n2 = commit_pass2(V, C, E, kp, guard)
+    return D, E, Cn, (0, n2)
+
+
+def commit_pass2(V, C, E, kp, guard=False):
+    """Pass 2, C - V E, from the digits of V (row scales) and of E (column
+    scales); with guard=True the elements its guard flags are recomputed in
+    FP64.  Returns the updated C and the number of such elements."""
+    L, nb = C.shape
+    Er = [max(ebound(v) for v in V[r, :kp]) for r in range(L)]
+    a = [[digits(V[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
     Ee = [max(ebound(E[t, c]) for t in range(kp)) for c in range(nb)]
     dE = [[digits(E[t, c], 56 - Ee[c]) for c in range(nb)] for t in range(kp)]
     Cn = C.copy()
+    n2 = 0
     for r in range(L):
         for c in range(nb):
             lev = levels(a[r], [dE[t][c] for t in range(kp)])
@@ -82,7 +159,16 @@ def commit_digits(V, C, T, kp):
             u = sum(lev[l] << (43 - 7 * l) for l in range(7)) + (lev[7] >> 6) + (lev[8] >> 13)
             assert abs(u) < 2 ** 63
             Cn[r, c] = float(F(C[r, c]) - F(float(u)) * F(2) ** (Er[r] + Ee[c] - 57))
-    return D, E, Cn
+            if guard:
+                g = sum(abs(a[r][t][0]) * abs(dE[t][c][0]) for t in range(kp))
+                g += 2.0 ** 14 * abs(C[r, c]) * 2.0 ** (-(Er[r] + Ee[c]))
+                if not g >= 3072:
+                    x = C[r, c]
+                    for t in range(kp):
+                        x = x - V[r, t] * E[t, c]
+                    Cn[r, c] = x
+                    n2 += 1
+    return Cn, n2
 
 
 def test_digit_products_as_accurate_as_fp64():
@@ -96,7 +182,7 @@ def test_digit_products_as_accurate_as_fp64():
         C = rng.standard_normal((L, nb))
         C[5, 1] = 0.0
         T = np.triu(rng.standard_normal((kp, kp)))
-        D, E, Cn = commit_digits(V, C, T, kp)
+        D, E, Cn, _ = commit_digits(V, C, T, kp)
         D64 = V.T @ C
         Dx = [[sum(F(V[r, t]) * F(C[r, c]) for r in range(L)) for c in range(nb)] for t in range(kp)]
         scale = np.abs(V).T @ np.abs(C)
@@ -120,3 +206,90 @@ def test_digit_split_is_exact_for_representable_values():
         d = digits(x, 56 - E)
         y = sum(abs(v) << (49 - 7 * k) for k, v in enumerate(d))
         assert F(y) * F(2) ** (E - 56) == abs(F(x))
+
+
+def gamma(k):
+    u = 2.0 ** -53
+    return k * u / (1 - k * u)
+
+
+def check_against_fp64_bound(V, C, T, kp, guard):
+    """Errors of the digit commit (with or without its guard) relative to
+    the worst-case bounds of the FP64 evaluation, element by element:
+    |D - D_exact| / (gamma_L sum |v||c|) and
+    |C' - C'_exact| / (gamma_(k+1) (|c| + sum |v||e|) + u |C'|)."""
+    L, nb = C.shape
+    D, E, Cn, counts = commit_digits(V, C, T, kp, guard=guard)
+    Dx = [[sum(F(V[r, t]) * F(C[r, c]) for r in range(L)) for c in range(nb)] for t in range(kp)]
+    b1 = gamma(L) * (np.abs(V).T @ np.abs(C))
+    r1 = max(abs(float(F(D[t, c]) - Dx[t][c])) / b1[t, c] for t in range(kp) for c in range(nb))
+    Cx = [[F(C[r, c]) - sum(F(V[r, t]) * F(E[t, c]) for t in range(kp)) for c in range(nb)] for r in range(L)]
+    b2 = gamma(kp + 1) * (np.abs(V) @ np.abs(E) + np.abs(C)) + 2.0 ** -53 * np.abs(Cn)
+    r2 = max(abs(float(F(Cn[r, c]) - Cx[r][c])) / b2[r, c] for r in range(L) for c in range(nb))
+    return r1, r2, counts
+
+
+def triangular_V(rng, L, kp):
+    V = rng.standard_normal((L, kp))
+    for t in range(kp):
+        V[:t, t] = 0.0
+    return V
+
+
+def test_guard_catches_large_entry_paired_with_zero():
+    """C's first row scaled by 2^30 while V(0, t) = 0 for t >= 1 (the zero
+    triangle of the reflectors): the column scale is set by a row that does
+    not take part in D(t >= 1, c), so the unguarded digits lose ~30 bits of
+    those sums (far outside the FP64 bound); the guard fires and the result
+    is back within it."""
+    rng = np.random.default_rng(3)
+    L, kp, nb = 36, 7, 3
+    V = triangular_V(rng, L, kp)
+    C = rng.standard_normal((L, nb))
+    C[0, :] *= 2.0 ** 30
+    T = np.triu(rng.standard_normal((kp, kp)))
+    r1, _, _ = check_against_fp64_bound(V, C, T, kp, guard=False)
+    assert r1 > 1e3
+    r1, r2, counts = check_against_fp64_bound(V, C, T, kp, guard=True)
+    assert counts[0] == 1 and r1 <= 1.0 and r2 <= 1.0
+
+
+def test_guard_catches_mismatched_scales_in_pass2():
+    """Pass 2 alone: rows of V dominated by reflector 0 where D'(0, :) is
+    tiny and D'(t >= 1, :) large, and small entries of C: every product
+    V(r, t) D'(t, c) and x itself lie far below 2^(Er + Ee), so the digits
+    lose bits; the pass-2 guard recomputes those elements in FP64 and every
+    element is within the FP64 bound again."""
+    rng = np.random.default_rng(4)
+    L, kp, nb = 40, 6, 2
+    V = triangular_V(rng, L, kp)
+    V[:, 1:] *= 2.0 ** -30
+    E = rng.standard_normal((kp, nb))
+    E[0, :] *= 2.0 ** -40
+    C = 2.0 ** -45 * rng.standard_normal((L, nb))
+
+    def ratio(Cn):
+        Cx = [[F(C[r, c]) - sum(F(V[r, t]) * F(E[t, c]) for t in range(kp)) for c in range(nb)] for r in range(L)]
+        b2 = gamma(kp + 1) * (np.abs(V) @ np.abs(E) + np.abs(C)) + 2.0 ** -53 * np.abs(Cn)
+        return max(abs(float(F(Cn[r, c]) - Cx[r][c])) / b2[r, c] for r in range(L) for c in range(nb))
+
+    assert ratio(commit_pass2(V, C, E, kp)[0]) > 1e3
+    Cn, n2 = commit_pass2(V, C, E, kp, guard=True)
+    assert n2 > 0 and ratio(Cn) <= 1.0
+
+
+def test_guard_is_quiet_on_ordinary_operands_long_panel():
+    """L = 300 (so pass 1 moves its level sums into int32 twice and keeps
+    levels 7-8 in FP32 across the blocks), rows of V and C scaled together
+    over 2^-20 .. 2^20: the guard never sends the batch to FP64 and every
+    element of both passes is within the FP64 bound."""
+    rng = np.random.default_rng(5)
+    L, kp, nb = 300, 12, 2
+    V = triangular_V(rng, L, kp)
+    rs = 2.0 ** rng.integers(-20, 21, size=(L, 1))
+    V *= rs
+    C = rng.standard_normal((L, nb)) * rs
+    T = np.triu(rng.standard_normal((kp, kp))) / 4
+    r1, r2, counts = check_against_fp64_bound(V, C, T, kp, guard=True)
+    assert counts[0] == 0
+    assert r1 <= 1.0 and r2 <= 1.0
