@@ -16,7 +16,7 @@ constexpr int ROT_STAGE = 2048;          // rotations staged per pass
 // guard's fallback): x - sum_t V(row, t) E(t), in the order of the FP64
 // commit, with V row-major (ld KM, reflector t zero above row t and v0 on
 // row t) and E = column c of D' (stride CB).  Out of line: it is rare.
-__device__ __noinline__ double commit_elem_fp64(const double* V, const double* vtop, const double* E, int kp, int row,
+static __device__ __noinline__ double commit_elem_fp64(const double* V, const double* vtop, const double* E, int kp, int row,
                                                 double x, int* counter) {
   for (int t = 0; t < kp; ++t) {
     const double vt = (row > t) ? __ldcg(V + (size_t)row * KM + t) : ((row == t) ? vtop[t] : 0.0);
