@@ -305,10 +305,10 @@ int lhdm_set_wait_limit(lhdm_ctx* ctx, int64_t ns);
  * products of the block reflector update formed from exact 7-bit digit
  * products on bf16 tensor cores, with a fallback to FP64 where the digits
  * could be less accurate than an FP64 evaluation): mode 1 sends every batch
- * of the later solves on ctx to the FP64 path as the guard would, mode 2
- * recomputes every element of pass 2 in FP64, mode 0 restores the guard's
- * own decisions.  Results must not change beyond rounding; the counts are
- * in the "ctl" words of lhdm_debug_state.  Errors: INVALID_ARG.
+ * of the later solves on ctx to the FP64 path as the guard would, mode 0
+ * restores the guard's own decisions.  Results must not change beyond
+ * rounding; the count of batches sent is word [10] of the "ctl" state of
+ * lhdm_debug_state.  Errors: INVALID_ARG.
  */
 int lhdm_debug_commit_guard(lhdm_ctx* ctx, int32_t mode);
 
@@ -337,8 +337,8 @@ int lhdm_trace(lhdm_ctx* ctx, int32_t* out, int32_t max_rows, void* stream);
  * (length m), "yP", "xP", "order", "rslot" (positions), "pos" (columns),
  * "W" (ld = max_m rounded up to even), "R" (slot-major, ld = the context's
  * min(max_m, max_n) rounded up to even), "ctl" (16 int32 control words;
- * [10] = commit batches and [11] = commit elements that the accuracy guard
- * of the tensor-core commit sent to FP64).  FP64 except the int32 arrays.  Errors: INVALID_ARG for an unknown name or count too large. */
+ * [10] = commit batches that the accuracy guard of the tensor-core commit
+ * sent to FP64).  FP64 except the int32 arrays.  Errors: INVALID_ARG for an unknown name or count too large. */
 int lhdm_debug_state(lhdm_ctx* ctx, const char* name, void* host, int64_t count, void* stream);
 
 /* Profile of the last solve on ctx.  ms[0..12) = device time in ms of each

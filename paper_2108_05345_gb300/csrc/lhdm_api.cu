@@ -492,7 +492,7 @@ int lhdm_set_wait_limit(lhdm_ctx* c, int64_t ns) {
 }
 
 int lhdm_debug_commit_guard(lhdm_ctx* c, int32_t mode) {
-  if (!c || mode < 0 || mode > 2) return LHDM_ERR_INVALID_ARG;
+  if (!c || mode < 0 || mode > 1) return LHDM_ERR_INVALID_ARG;
   c->guard_force = mode;
   return LHDM_OK;
 }

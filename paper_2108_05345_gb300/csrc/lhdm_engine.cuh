@@ -129,14 +129,13 @@ struct Inst {
   int bar_extra;              // failure-detection test: arrivals the grid barrier
                               // expects beyond the grid (0 in every normal solve)
   int guard_force;            // test aid: 1 sends every tensor-core commit batch to
-                              // FP64, 2 every pass-2 element (0 in normal solves)
+                              // FP64 as the accuracy guard would (0 in normal solves)
   DevParams prm;
 };
 
 // control words (ctl[])
 enum { C_KP = 0, C_DROPS, C_CAND, C_NROT, C_NRUN, C_READY, C_STATUS, C_ERR, C_KK, C_NFLIP,
-       C_GUARD1,   // commit batches the accuracy guard handed to the FP64 path
-       C_GUARD2 }; // commit elements it recomputed in FP64
+       C_GUARD1 }; // commit batches the accuracy guard handed to the FP64 path
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -277,6 +276,12 @@ __device__ __forceinline__ unsigned dig2(unsigned wa, unsigned wb, int sh, unsig
   const unsigned p = ((wa >> sh) & 0x7Fu) | (((wb >> sh) & 0x7Fu) << 16) | 0x43004300u;
   unsigned r;
   asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(p), "r"(sg), "r"(nb));
+  return r;
+}
+// a bf16 pair times 2^-7 (exact for the 7-bit digits: no bits are lost)
+__device__ __forceinline__ unsigned bf16x2_scale_m7(unsigned x) {
+  unsigned r;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0x3C003C00u), "r"(0x80008000u));
   return r;
 }
 // digit k (0..7) of a value given as 28-bit halves

@@ -12,20 +12,6 @@ constexpr int CAND_LOCAL_MAX = 2048;     // local DM candidates per CTA
 constexpr int CAND_STAGE = 4096;         // merged candidates staged per pass
 constexpr int ROT_STAGE = 2048;          // rotations staged per pass
 
-// One element of the tensor-core commit's pass 2 in FP64 (its accuracy
-// guard's fallback): x - sum_t V(row, t) E(t), in the order of the FP64
-// commit, with V row-major (ld KM, reflector t zero above row t and v0 on
-// row t) and E = column c of D' (stride CB).  Out of line: it is rare.
-static __device__ __noinline__ double commit_elem_fp64(const double* V, const double* vtop, const double* E, int kp, int row,
-                                                double x, int* counter) {
-  for (int t = 0; t < kp; ++t) {
-    const double vt = (row > t) ? __ldcg(V + (size_t)row * KM + t) : ((row == t) ? vtop[t] : 0.0);
-    x = fma(-vt, E[t * 16], x);
-  }
-  atomicAdd(counter, 1);
-  return x;
-}
-
 // Orderable key of a positive double (dual values of DM candidates are > 0).
 __device__ __forceinline__ unsigned long long wkey(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -1000,7 +986,10 @@ struct Engine {
     if (I.Vd != nullptr && kk > 4 && kk <= 32) {
       for (int rr = warp; rr < nr; rr += NW) {
         const int row = q0 + rr;
-        const double v = (lane < kk) ? (row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0)) : 0.0;
+        // reflector lane scaled by 2^-Ft, 2^Ft > |v0| >= |V(:, lane)|
+        const double v = (lane < kk) ? scale2(row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0),
+                                              -ebound(s_v0[lane]))
+                                     : 0.0;
         const int er = __reduce_max_sync(0xffffffffu, ebound(v));
         unsigned ha, la;
         halves28(fix56(v, 56 - er), ha, la);
@@ -1767,31 +1756,35 @@ struct Engine {
   //    its rows (exact: at most 8 pairs of products below 2^14 per row).
   //  D' = T^T D in FP64.
   //  pass 2: C -= V D'.  128-row chunks, double-buffered.  From the digits
-  //    of V (row scale) and of D' (column scale 2^Ee) warp (row tile, column
-  //    tile) forms the 9 level sums of its 16 x 8 tile (exact in FP32: at
-  //    most 8 pairs x 32 terms), combines them in int64
+  //    of V (row scale) and of D'' = 2^Ft D' (column scale 2^Ee) warp (row
+  //    tile, column tile) forms the 9 level sums of its 16 x 8 tile (exact
+  //    in FP32: at most 8 pairs x 32 terms), combines them in int64
   //    (u = sum_lam lev_lam 2^(43-7 lam), levels 7 and 8 rounded down;
   //    |u| < 2^63 as lev_lam < (lam+1) 2^19) and applies x -= u 2^(Er+Ee-57)
   //    and the trailing norm in FP64.
+  //  Reflector scales: V's digits are of V(r, t) / 2^Ft with 2^Ft > |v0_t|
+  //    >= |V(:, t)| (the panel scales each reflector by its own power of
+  //    two before the row scale is taken), so reflectors of very different
+  //    norms - later columns of a correlated block keep little of their
+  //    norm after the earlier reflectors - keep all their digits; the factor
+  //    2^Ft returns in D (pass 1) and in D'' (pass 2).
   // Every sum is exact or in a fixed order, so the result is bitwise
   // reproducible.  Shared memory (bytes of the work area): V digit buffers
   // [0, 64K) and [64K, 128K) (R rows of 512 B: the ND digit planes side by
   // side, 16-byte chunks XOR-swizzled by row so that ldmatrix is
   // conflict-free), pass-1 C' digit buffers in the upper halves of those
   // (pass 1 has R = 64), D' digits at 128K.
-  // Accuracy guard of the digit products.  The fixed-point digits carry 56
-  // bits under one power-of-two scale per V row and per column of C' (pass 1)
-  // or D' (pass 2), so a sum whose terms are all far below the scale loses
-  // bits that an FP64 dot product would keep.  Each pass therefore also forms
-  // the sum of |leading digit| products (one more MMA per step, exact
-  // integers): a lower bound of sum |v||c| in units of 2^(scale - 14).  The
-  // digit result's error is at most 2L 2^(Ec-57) in pass 1 and
-  // (3k+2) 2^(Er+Ee-57) in pass 2; where that could exceed the worst-case
-  // bound of the FP64 evaluation, gamma_L sum |v||c| (pass 1) or
-  // gamma_(k+1) (|x| + sum |v||e|) (pass 2), the FP64 path takes over: the
-  // whole batch (pass 1, before C is touched) or the single element (pass 2).
-  static constexpr float GUARD1 = 2048.0f;  // 2^11: sum |v||c| >= 2^(Ec-3)
-  static constexpr double GUARD2 = 3072.0;  // 3 * 2^10: |x| + sum |v||e| >= 3 * 2^(Er+Ee-4)
+  // Accuracy guard of pass 1.  The fixed-point digits carry 56 bits under
+  // one power-of-two scale per V row and per column of C', so a sum whose
+  // terms all lie far below the scale (a large entry of C paired with zeros
+  // of V, say) loses bits that an FP64 dot product would keep.  Pass 1 also
+  // forms the sum of |leading digit| products (one more MMA per step, exact
+  // integers), a lower bound of sum |v'||c'| in units of 2^(Ec - 14).  The
+  // digit result's error is at most 2L 2^(Ec-57) (times 2^Ft); where that
+  // could exceed the worst-case bound of the FP64 evaluation,
+  // gamma_L sum |v||c|, i.e. where the sum stays below 2^11, the batch goes
+  // to the FP64 commit before any column is touched.
+  static constexpr float GUARD1 = 2048.0f;  // 2^11: sum |v'||c'| >= 2^(Ec-3)
   static constexpr unsigned ABS2 = 0x7FFF7FFFu;  // clears the signs of a bf16 pair
 
   // Returns 0 when the batch is committed, 1 when a bounded wait expired, 2
@@ -2047,7 +2040,7 @@ struct Engine {
       const int t = o / nb, c = o - t * nb;
       double s = sL[((NLV - 1) * 32 + t) * NBP + c];
       for (int lam = NLV - 2; lam >= 0; --lam) s = fma(s, 0x1p-7, sL[(lam * 32 + t) * NBP + c]);
-      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14);
+      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14 + ebound(cs.s_vt[t]));  // 2^Ft: the reflector's scale
     }
     __syncthreads();
     // D' = T^T D
@@ -2060,7 +2053,7 @@ struct Engine {
     __syncthreads();
     // digits of D' under a column scale: warp c, lane t
     for (int c = warp; c < NBP; c += NW) {
-      const double v = (c < nb && lane < kp) ? cs.s_E[lane * CB + c] : 0.0;
+      const double v = (c < nb && lane < kp) ? scale2(cs.s_E[lane * CB + c], ebound(cs.s_vt[lane])) : 0.0;
       const int ee = __reduce_max_sync(0xffffffffu, ebound(v));
       unsigned ha, la;
       halves28(fix56(v, 56 - ee), ha, la);
@@ -2092,7 +2085,7 @@ struct Engine {
       const bool okv = wait_v(b);
       if (__syncthreads_or(!okv)) {
         expired();
-        return 1;
+        return false;
       }
       if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
@@ -2110,7 +2103,6 @@ struct Engine {
         for (int l = 0; l < NLV; ++l)
 #pragma unroll
           for (int j = 0; j < 4; ++j) a2[l][j] = 0.f;
-        float g2[4] = {0.f, 0.f, 0.f, 0.f};  // sum of |leading digit| products (guard)
         const unsigned short* sAb = sV + b * BUF;
         const int r0 = rt * 16, rq = r0 + (lane & 7) + ((lane >> 3) & 1) * 8;
 #pragma unroll
@@ -2125,11 +2117,6 @@ struct Engine {
             ldsm_x4(a, vaddr(sAb, R2, k, rq, ks * 2 + ((lane >> 4) & 1)));
 #pragma unroll
             for (int l = 0; l < ND && k + l < NLV; ++l) mma_bf16(a2[k + l], a, eb[l]);
-            if (k == 0) {
-              const unsigned ga[4] = {a[0] & ABS2, a[1] & ABS2, a[2] & ABS2, a[3] & ABS2};
-              const unsigned gb[2] = {eb[0][0] & ABS2, eb[0][1] & ABS2};
-              mma_bf16(g2, ga, gb);
-            }
           }
         }
 #pragma unroll
@@ -2143,14 +2130,8 @@ struct Engine {
             for (int l = 0; l < 7; ++l) u += (long long)__float2int_rn(a2[l][j]) * (1ll << (43 - 7 * l));
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
-            const int esc = ((j < 2) ? er0 : er1) + s_Ee[c];  // exponent of the product scale
-            const int es = max(-2044, esc - 57);
-            double x = xv[j] - scale2((double)u, es);
-            // guard of pass 2: 2^14 |x| / 2^(Er+Ee) + sum |leading digit
-            // products| below GUARD2 -> this element in FP64, in the order of
-            // the FP64 commit
-            if (I.guard_force == 2 || !((double)g2[j] + scale2(fabs(xv[j]), max(-2044, min(2044, 14 - esc))) >= GUARD2))
-              x = commit_elem_fp64(I.V, cs.s_vt, cs.s_E + c, kp, row, xv[j], I.ctl + C_GUARD2);
+            const int es = max(-2044, ((j < 2) ? er0 : er1) + s_Ee[c] - 57);
+            const double x = xv[j] - scale2((double)u, es);
             p[row] = x;
             if (row >= kp) {
               if (j & 1) nrm1 = fma(x, x, nrm1);
@@ -2269,7 +2250,7 @@ struct Engine {
   // reflector I - V T^T V^T applied to the trailing rows of every Z column
   // and of Q^T b, and u = ||C|| for the Z columns (Algorithm 3, rank-k update
   // and column norms of C).
-  __device__ bool commit(const int* s_J) {
+  __device__ __forceinline__ bool commit(const int* s_J) {
     const int L = I.m - nP;
     flops(PH_COMMIT, 4.0 * kp * (double)L * (double)(I.n - nP - kp + 1) + 2.0 * (double)L * (I.n - nP - kp));
     // (a) R columns of the new positions (free slots rslot[nP..nP+kp))
@@ -3122,7 +3103,7 @@ struct Engine {
   }
 
   // ------------------------------------------------------------ the solve
-  __device__ void run() {
+  __device__ __forceinline__ void run() {
     phase(PH_SETUP);
     setup();
     flops(PH_SETUP, 4.0 * (double)I.m * I.n);

@@ -3,21 +3,26 @@ restatement, exact integers).
 
 The CUDA commit forms D = V^T C and C - V E from 56-bit fixed-point digits:
 a value x with |x| < 2^E is Y = round(|x| 2^(56-E)), cut into eight 7-bit
-digits; V rows carry a row scale 2^Er, C' = 2^Er C and E carry column
-scales; products of digits are summed per level k + l <= 8 exactly, and the
-levels are recombined (pass 2 in int64 with levels 7 and 8 rounded down).
+digits; reflector t of V is first scaled by 2^-Ft (2^Ft > |v0_t|, its pivot
+entry), then V rows carry a row scale 2^Er, C' = 2^Er C and E'' = 2^Ft E
+carry column scales; products of digits are summed per level k + l <= 8
+exactly, and the levels are recombined (pass 2 in int64 with levels 7 and 8
+rounded down).
 This test restates those steps in Python integers (with the FP32 and int32
 accumulation of the level sums as the kernel does it: 16-row MMA steps,
 levels 0-6 moved into int32 every 128 rows, levels 7-8 kept in FP32) and
 checks the result against the exact (rational) product.
 
-The fixed point is accurate relative to the column scale, not to each
-term: where every term of a sum lies far below the scale (a large entry of
-C paired with a zero of V, say), the digits lose bits an FP64 dot product
-keeps.  The kernel's accuracy guard (sum of |leading digit| products, one
-more MMA) detects that and hands the batch (pass 1) or the element (pass 2)
-to FP64; with the guard the result is within the worst-case bound of the
-FP64 evaluation, gamma_L sum |v||c|, element by element.
+The fixed point is accurate relative to the scales, not to each term:
+where every term of a sum lies far below them (a large entry of C paired
+with a zero of V, say), the digits lose bits an FP64 dot product keeps.
+The reflector scales remove the common case (reflectors of very different
+norms); pass 1's accuracy guard (sum of |leading digit| products, one more
+MMA) detects the rest and hands the batch to FP64, so D is within the
+worst-case bound of the FP64 evaluation, gamma_L sum |v||c|, element by
+element.  Pass 2 has no guard: its error is at most (3k+2) 2^(Er+Ee-57) per
+element, within the FP64 bound unless every product of the element lies
+far below both its row and its column scale.
 """
 import math
 import struct
@@ -102,13 +107,22 @@ def guard_pass1(a, bC, kp, nb):
                      for t in range(kp)], dtype=float)
 
 
+def reflector_scales(V, kp):
+    """Ft = exponent bound of reflector t's largest entry (for a Householder
+    vector that is its pivot entry v0, |v0| = |x0| + ||x|| >= |x_r|, which
+    the kernel uses)."""
+    return [max(ebound(v) for v in V[:, t]) for t in range(kp)]
+
+
 def commit_digits(V, C, T, kp, guard=False):
-    """The tensor-core commit restated; with guard=True its accuracy guard
-    too (FP64 for the whole batch when pass 1's guard fires, for an element
-    when pass 2's does).  Returns D, E, the updated C and the guard counts."""
+    """The tensor-core commit restated; with guard=True pass 1's accuracy
+    guard too (FP64 for the whole batch when it fires).  Returns D, E, the
+    updated C and the number of batches sent to FP64 (0 or 1)."""
     L, nb = V.shape[0], C.shape[1]
-    Er = [max(ebound(v) for v in V[r, :kp]) for r in range(L)]
-    a = [[digits(V[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
+    Ft = reflector_scales(V, kp)
+    Vs = np.array([[math.ldexp(V[r, t], -Ft[t]) for t in range(kp)] for r in range(L)])
+    Er = [max(ebound(v) for v in Vs[r, :kp]) for r in range(L)]
+    a = [[digits(Vs[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
     Ec = [max([ebound(C[r, c]) + Er[r] for r in range(L) if ebound(C[r, c]) > -2000] or [-8000]) for c in range(nb)]
     bC = [[digits(C[r, c], Er[r] + 56 - Ec[c]) for c in range(nb)] for r in range(L)]
     if guard and (guard_pass1(a, bC, kp, nb) < 2048).any():
@@ -127,7 +141,7 @@ def commit_digits(V, C, T, kp, guard=False):
                 for t in range(kp):
                     x = x - V[r, t] * E[t, c]
                 Cn[r, c] = x
-        return D, E, Cn, (1, 0)
+        return D, E, Cn, 1
     D = np.zeros((kp, nb))
     for t in range(kp):
         for c in range(nb):
@@ -135,23 +149,23 @@ def commit_digits(V, C, T, kp, guard=False):
             s = float(lev[ND])
             for lam in range(ND - 1, -1, -1):
                 s = s * 2.0 ** -7 + lev[lam]
-            D[t, c] = math.ldexp(s, Ec[c] - 14)
+            D[t, c] = math.ldexp(s, Ec[c] - 14 + Ft[t])
     E = T[:kp, :kp].T @ D
-    Cn, n2 = commit_pass2(V, C, E, kp, guard)
-    return D, E, Cn, (0, n2)
+    return D, E, commit_pass2(V, C, E, kp), 0
 
 
-def commit_pass2(V, C, E, kp, guard=False):
-    """Pass 2, C - V E, from the digits of V (row scales) and of E (column
-    scales); with guard=True the elements its guard flags are recomputed in
-    FP64.  Returns the updated C and the number of such elements."""
+def commit_pass2(V, C, E, kp):
+    """Pass 2, C - V E, from the digits of V / 2^Ft (row scales) and of
+    E'' = 2^Ft E (column scales)."""
     L, nb = C.shape
-    Er = [max(ebound(v) for v in V[r, :kp]) for r in range(L)]
-    a = [[digits(V[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
-    Ee = [max(ebound(E[t, c]) for t in range(kp)) for c in range(nb)]
-    dE = [[digits(E[t, c], 56 - Ee[c]) for c in range(nb)] for t in range(kp)]
+    Ft = reflector_scales(V, kp)
+    Vs = np.array([[math.ldexp(V[r, t], -Ft[t]) for t in range(kp)] for r in range(L)])
+    Er = [max(ebound(v) for v in Vs[r, :kp]) for r in range(L)]
+    a = [[digits(Vs[r, t], 56 - Er[r]) for t in range(kp)] for r in range(L)]
+    Es = np.array([[math.ldexp(E[t, c], Ft[t]) for c in range(nb)] for t in range(kp)])
+    Ee = [max(ebound(Es[t, c]) for t in range(kp)) for c in range(nb)]
+    dE = [[digits(Es[t, c], 56 - Ee[c]) for c in range(nb)] for t in range(kp)]
     Cn = C.copy()
-    n2 = 0
     for r in range(L):
         for c in range(nb):
             lev = levels(a[r], [dE[t][c] for t in range(kp)])
@@ -159,16 +173,7 @@ def commit_pass2(V, C, E, kp, guard=False):
             u = sum(lev[l] << (43 - 7 * l) for l in range(7)) + (lev[7] >> 6) + (lev[8] >> 13)
             assert abs(u) < 2 ** 63
             Cn[r, c] = float(F(C[r, c]) - F(float(u)) * F(2) ** (Er[r] + Ee[c] - 57))
-            if guard:
-                g = sum(abs(a[r][t][0]) * abs(dE[t][c][0]) for t in range(kp))
-                g += 2.0 ** 14 * abs(C[r, c]) * 2.0 ** (-(Er[r] + Ee[c]))
-                if not g >= 3072:
-                    x = C[r, c]
-                    for t in range(kp):
-                        x = x - V[r, t] * E[t, c]
-                    Cn[r, c] = x
-                    n2 += 1
-    return Cn, n2
+    return Cn
 
 
 def test_digit_products_as_accurate_as_fp64():
@@ -213,20 +218,20 @@ def gamma(k):
     return k * u / (1 - k * u)
 
 
-def check_against_fp64_bound(V, C, T, kp, guard):
-    """Errors of the digit commit (with or without its guard) relative to
-    the worst-case bounds of the FP64 evaluation, element by element:
+def bound_ratios(V, C, T, kp, guard):
+    """Errors of the digit commit (with or without pass 1's guard) relative
+    to the worst-case bounds of the FP64 evaluation, element by element:
     |D - D_exact| / (gamma_L sum |v||c|) and
     |C' - C'_exact| / (gamma_(k+1) (|c| + sum |v||e|) + u |C'|)."""
     L, nb = C.shape
-    D, E, Cn, counts = commit_digits(V, C, T, kp, guard=guard)
+    D, E, Cn, fb = commit_digits(V, C, T, kp, guard=guard)
     Dx = [[sum(F(V[r, t]) * F(C[r, c]) for r in range(L)) for c in range(nb)] for t in range(kp)]
     b1 = gamma(L) * (np.abs(V).T @ np.abs(C))
     r1 = max(abs(float(F(D[t, c]) - Dx[t][c])) / b1[t, c] for t in range(kp) for c in range(nb))
     Cx = [[F(C[r, c]) - sum(F(V[r, t]) * F(E[t, c]) for t in range(kp)) for c in range(nb)] for r in range(L)]
     b2 = gamma(kp + 1) * (np.abs(V) @ np.abs(E) + np.abs(C)) + 2.0 ** -53 * np.abs(Cn)
     r2 = max(abs(float(F(Cn[r, c]) - Cx[r][c])) / b2[r, c] for r in range(L) for c in range(nb))
-    return r1, r2, counts
+    return r1, r2, fb
 
 
 def triangular_V(rng, L, kp):
@@ -248,34 +253,55 @@ def test_guard_catches_large_entry_paired_with_zero():
     C = rng.standard_normal((L, nb))
     C[0, :] *= 2.0 ** 30
     T = np.triu(rng.standard_normal((kp, kp)))
-    r1, _, _ = check_against_fp64_bound(V, C, T, kp, guard=False)
+    r1, _, _ = bound_ratios(V, C, T, kp, guard=False)
     assert r1 > 1e3
-    r1, r2, counts = check_against_fp64_bound(V, C, T, kp, guard=True)
-    assert counts[0] == 1 and r1 <= 1.0 and r2 <= 1.0
+    r1, r2, fb = bound_ratios(V, C, T, kp, guard=True)
+    assert fb == 1 and r1 <= 1.0 and r2 <= 1.0
 
 
-def test_guard_catches_mismatched_scales_in_pass2():
-    """Pass 2 alone: rows of V dominated by reflector 0 where D'(0, :) is
-    tiny and D'(t >= 1, :) large, and small entries of C: every product
-    V(r, t) D'(t, c) and x itself lie far below 2^(Er + Ee), so the digits
-    lose bits; the pass-2 guard recomputes those elements in FP64 and every
-    element is within the FP64 bound again."""
+def test_reflectors_of_different_norms():
+    """Reflectors whose norms differ by 2^30 (later columns of a correlated
+    block keep little of their norm): without the reflector scales the rows
+    of V would be set by the large reflectors and the small ones would lose
+    30 bits in both passes; with them both passes stay within the FP64
+    bounds and the guard stays quiet."""
     rng = np.random.default_rng(4)
     L, kp, nb = 40, 6, 2
     V = triangular_V(rng, L, kp)
     V[:, 1:] *= 2.0 ** -30
+    C = rng.standard_normal((L, nb))
+    T = np.diag(2.0 / np.sum(V * V, axis=0))  # beta_t = 2 / ||v_t||^2 scales like the reflector
+    r1, r2, fb = bound_ratios(V, C, T, kp, guard=True)
+    assert fb == 0 and r1 <= 1.0 and r2 <= 1.0
+
+
+def test_pass2_bound_on_mismatched_scales():
+    """The pattern pass 2 does not guard: in every row the largest scaled
+    reflector entry meets a tiny D'' entry and the large D'' entries meet
+    tiny reflector entries.  The element error then exceeds the FP64 bound,
+    but stays within the stated (3k+2) 2^(Er+Ee-57)."""
+    rng = np.random.default_rng(6)
+    L, kp, nb = 40, 4, 2
+    V = triangular_V(rng, L, kp)
+    V[kp:, 1:] *= 2.0 ** -20  # rows below the triangle dominated by reflector 0
     E = rng.standard_normal((kp, nb))
-    E[0, :] *= 2.0 ** -40
+    E[0, :] *= 2.0 ** -20     # ... where E is tiny
     C = 2.0 ** -45 * rng.standard_normal((L, nb))
-
-    def ratio(Cn):
-        Cx = [[F(C[r, c]) - sum(F(V[r, t]) * F(E[t, c]) for t in range(kp)) for c in range(nb)] for r in range(L)]
-        b2 = gamma(kp + 1) * (np.abs(V) @ np.abs(E) + np.abs(C)) + 2.0 ** -53 * np.abs(Cn)
-        return max(abs(float(F(Cn[r, c]) - Cx[r][c])) / b2[r, c] for r in range(L) for c in range(nb))
-
-    assert ratio(commit_pass2(V, C, E, kp)[0]) > 1e3
-    Cn, n2 = commit_pass2(V, C, E, kp, guard=True)
-    assert n2 > 0 and ratio(Cn) <= 1.0
+    Cn = commit_pass2(V, C, E, kp)
+    Ft = reflector_scales(V, kp)
+    Vs = np.array([[math.ldexp(V[r, t], -Ft[t]) for t in range(kp)] for r in range(L)])
+    Er = [max(ebound(v) for v in Vs[r]) for r in range(L)]
+    Es = np.array([[math.ldexp(E[t, c], Ft[t]) for c in range(nb)] for t in range(kp)])
+    Ee = [max(ebound(Es[t, c]) for t in range(kp)) for c in range(nb)]
+    worst = 0.0
+    for r in range(L):
+        for c in range(nb):
+            exact = F(C[r, c]) - sum(F(V[r, t]) * F(E[t, c]) for t in range(kp))
+            err = abs(float(F(Cn[r, c]) - exact))
+            assert err <= (3 * kp + 2) * 2.0 ** (Er[r] + Ee[c] - 57) + 2.0 ** -53 * abs(Cn[r, c])
+            fp64 = gamma(kp + 1) * (abs(C[r, c]) + float(np.abs(V[r]) @ np.abs(E[:, c])))
+            worst = max(worst, err / fp64)
+    assert worst > 1.0  # outside the FP64 bound: the documented limit of pass 2
 
 
 def test_guard_is_quiet_on_ordinary_operands_long_panel():
@@ -290,6 +316,6 @@ def test_guard_is_quiet_on_ordinary_operands_long_panel():
     V *= rs
     C = rng.standard_normal((L, nb)) * rs
     T = np.triu(rng.standard_normal((kp, kp))) / 4
-    r1, r2, counts = check_against_fp64_bound(V, C, T, kp, guard=True)
-    assert counts[0] == 0
+    r1, r2, fb = bound_ratios(V, C, T, kp, guard=True)
+    assert fb == 0
     assert r1 <= 1.0 and r2 <= 1.0

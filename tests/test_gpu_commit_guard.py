@@ -6,8 +6,8 @@ built to strain it, and its accuracy guard's FP64 fallbacks:
   C' = 2^Er C, whose digits pass 1 multiplies, span 2^-30 .. 2^30), at
   k_max 12 and 32 (also with columns scaled over 2^-2 .. 2^2);
 - a nearly dependent pair of columns inside the DM block;
-- the guard's fallbacks forced on (every batch to FP64, or every pass-2
-  element): the result must not move beyond rounding.
+- the guard's fallback forced on (every batch to FP64): the result must not
+  move beyond rounding.
 Bar: identical passive set, trace and counters, ||x - x_oracle|| <= 1e-10
 ||x_oracle||."""
 import numpy as np
@@ -67,7 +67,7 @@ def test_nearly_dependent_block(L, ctx):
     assert_parity(x, P, info, ref, trace=ctx.trace())
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1])
 def test_forced_fallbacks(L, ctx, mode):
     A, b = scaled(7, 12, 0)
     ref = O.nnls(A, b, k_max=24, trace=True)
@@ -77,5 +77,5 @@ def test_forced_fallbacks(L, ctx, mode):
         ctl = ctx.state("ctl", 16)
     finally:
         ctx.force_commit_guard(0)
-    assert ctl[10 if mode == 1 else 11] > 0  # the fallback ran
+    assert ctl[10] > 0  # the fallback ran
     assert_parity(x, P, info, ref, trace=ctx.trace())
