@@ -1799,6 +1799,11 @@ struct Engine {
     constexpr int SB = R1 + 8;             // row stride of C' digits (bf16)
     constexpr int SE = 40;                 // row stride of D' digits (bf16)
     const int L = cs.L;
+    // The digits cover rows [kp, L); the first kp rows (the reflectors'
+    // triangle: pivots and the zeros above them, whose row scales would
+    // outweigh every other row) are done in FP64.  Chunk rows below are
+    // counted from row kp.
+    const int Ld = L - kp;
     unsigned short* sV = reinterpret_cast<unsigned short*>(cs.wk);
     unsigned short* sE = sV + 2 * BUF;
     __shared__ int s_Ec[CB], s_Ee[CB];
@@ -1824,10 +1829,10 @@ struct Engine {
     __syncthreads();
     auto stage_v = [&](int rb, int R, int b) {
       unsigned short* dst = sV + b * BUF;
-      const int nr = min(R, L - rb);
+      const int nr = min(R, Ld - rb);
       if (tid == 0) {
         mbar_expect_tx(&s_mbar[b], (unsigned)(nr * 64 * ND));
-        bulk_g2s(dst, I.Vd + (size_t)rb * (16 * ND), (unsigned)(nr * 64 * ND), &s_mbar[b]);
+        bulk_g2s(dst, I.Vd + (size_t)(kp + rb) * (16 * ND), (unsigned)(nr * 64 * ND), &s_mbar[b]);
       }
       if (nr < R) {
         for (int e = nr * 4 * ND + tid; e < R * 4 * ND; e += NT)
@@ -1858,9 +1863,10 @@ struct Engine {
     __syncthreads();
     for (int p = warp; p < nb * 4; p += NW) {
       const int c = p >> 2;
-      const double* col = commit_col(cs.s_cid, c);
+      const double* col = commit_col(cs.s_cid, c) + kp;
+      const int* ver = I.Ver + kp;
       int lo, hi;
-      split(L, 4, p & 3, lo, hi);
+      split(Ld, 4, p & 3, lo, hi);
       int mx = -8000;
       for (int r0 = lo + lane; r0 < hi; r0 += 256) {
         double xv[8];
@@ -1869,7 +1875,7 @@ struct Engine {
         for (int u = 0; u < 8; ++u) {
           const int r = r0 + 32 * u;
           xv[u] = (r < hi) ? ldcg(col + r) : 0.0;
-          ev[u] = (r < hi) ? ldcg(I.Ver + r) : 0;
+          ev[u] = (r < hi) ? ldcg(ver + r) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -1882,7 +1888,7 @@ struct Engine {
     }
     __syncthreads();
     // ---- pass 1
-    const int nch1 = (L + R1 - 1) / R1;
+    const int nch1 = (Ld + R1 - 1) / R1;
     const bool mw = warp < MW;
     const int cmb = warp % COMBOS, sub = warp / COMBOS;
     const int mt = cmb % KT, nt = cmb / KT;
@@ -1898,10 +1904,10 @@ struct Engine {
       int* sR = reinterpret_cast<int*>(sC + NBP * R1);
       for (int e = tid; e < NBP * R1; e += NT) {
         const int c = e / R1, r = e - c * R1;
-        const bool ok = c < nb && rb + r < L;
-        cp8(sC + e, ok ? commit_col(cs.s_cid, c) + rb + r : I.u, ok);
+        const bool ok = c < nb && rb + r < Ld;
+        cp8(sC + e, ok ? commit_col(cs.s_cid, c) + kp + rb + r : I.u, ok);
       }
-      if (tid < R1) cp4(sR + tid, rb + tid < L ? I.Ver + rb + tid : I.Ver, rb + tid < L);
+      if (tid < R1) cp4(sR + tid, rb + tid < Ld ? I.Ver + kp + rb + tid : I.Ver, rb + tid < Ld);
       cp_commit();
     };
     auto digits_c = [&](int b) {
@@ -2040,7 +2046,11 @@ struct Engine {
       const int t = o / nb, c = o - t * nb;
       double s = sL[((NLV - 1) * 32 + t) * NBP + c];
       for (int lam = NLV - 2; lam >= 0; --lam) s = fma(s, 0x1p-7, sL[(lam * 32 + t) * NBP + c]);
-      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14 + ebound(cs.s_vt[t]));  // 2^Ft: the reflector's scale
+      // rows t .. kp-1 of the triangle in FP64 (V(r, t) = 0 above row t)
+      const double* col = commit_col(cs.s_cid, c);
+      double tri = 0.0;
+      for (int r = t; r < kp; ++r) tri = fma((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t], ldcg(col + r), tri);
+      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14 + ebound(cs.s_vt[t])) + tri;  // 2^Ft: the reflector's scale
     }
     __syncthreads();
     // D' = T^T D
@@ -2069,8 +2079,8 @@ struct Engine {
       if (lane == 0) s_Ee[c] = ee;
     }
     __syncthreads();
-    // ---- pass 2
-    const int nch2 = (L + R2 - 1) / R2;
+    // ---- pass 2 (digit rows kp .. L-1; the triangle rows after the loop)
+    const int nch2 = (Ld + R2 - 1) / R2;
     const bool act2 = warp < 8 * NTN;
     const int rt = warp & 7, nt2 = warp >> 3;
     const int c0 = nt2 * 8 + 2 * tq;
@@ -2085,12 +2095,12 @@ struct Engine {
       const bool okv = wait_v(b);
       if (__syncthreads_or(!okv)) {
         expired();
-        return false;
+        return 1;
       }
       if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
         // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
-        const int ra = rb + rt * 16 + g, rb8 = ra + 8;
+        const int ra = kp + rb + rt * 16 + g, rb8 = ra + 8;
         double xv[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -2140,6 +2150,15 @@ struct Engine {
           }
         }
       }
+    }
+    // the triangle rows r < kp in FP64, in the order of the FP64 commit
+    // (they are not part of the trailing norm)
+    for (int o = tid; o < kp * nb; o += NT) {
+      const int r = o / nb, c = o - r * nb;
+      double* col = commit_col(cs.s_cid, c);
+      double x = ldcg(col + r);
+      for (int t = 0; t <= r; ++t) x = fma(-((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t]), cs.s_E[t * CB + c], x);
+      col[r] = x;
     }
     // trailing norms: lanes of one column quad, then the 8 row tiles in order
 #pragma unroll
@@ -2313,7 +2332,7 @@ struct Engine {
     }
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     // the tensor-core form needs this panel's reflector digits
-    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 16384;  // int32 level sums
+    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 16384 && L >= kp + 64;  // int32 level sums
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
       __syncthreads();
