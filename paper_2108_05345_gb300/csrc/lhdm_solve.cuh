@@ -1799,11 +1799,13 @@ struct Engine {
     constexpr int SB = R1 + 8;             // row stride of C' digits (bf16)
     constexpr int SE = 40;                 // row stride of D' digits (bf16)
     const int L = cs.L;
-    // The digits cover rows [kp, L); the first kp rows (the reflectors'
-    // triangle: pivots and the zeros above them, whose row scales would
-    // outweigh every other row) are done in FP64.  Chunk rows below are
-    // counted from row kp.
-    const int Ld = L - kp;
+    // The digits cover rows [r0d, L); the first r0d rows - the reflectors'
+    // triangle (pivots and the zeros above them, whose row scales would
+    // outweigh every other row), rounded up to a multiple of 8 so that the
+    // staged digit rows keep the row swizzle of Vd - are done in FP64.
+    // Chunk rows below are counted from row r0d.
+    const int r0d = (kp + 7) & ~7;
+    const int Ld = L - r0d;
     unsigned short* sV = reinterpret_cast<unsigned short*>(cs.wk);
     unsigned short* sE = sV + 2 * BUF;
     __shared__ int s_Ec[CB], s_Ee[CB];
@@ -1832,7 +1834,7 @@ struct Engine {
       const int nr = min(R, Ld - rb);
       if (tid == 0) {
         mbar_expect_tx(&s_mbar[b], (unsigned)(nr * 64 * ND));
-        bulk_g2s(dst, I.Vd + (size_t)(kp + rb) * (16 * ND), (unsigned)(nr * 64 * ND), &s_mbar[b]);
+        bulk_g2s(dst, I.Vd + (size_t)(r0d + rb) * (16 * ND), (unsigned)(nr * 64 * ND), &s_mbar[b]);
       }
       if (nr < R) {
         for (int e = nr * 4 * ND + tid; e < R * 4 * ND; e += NT)
@@ -1863,8 +1865,8 @@ struct Engine {
     __syncthreads();
     for (int p = warp; p < nb * 4; p += NW) {
       const int c = p >> 2;
-      const double* col = commit_col(cs.s_cid, c) + kp;
-      const int* ver = I.Ver + kp;
+      const double* col = commit_col(cs.s_cid, c) + r0d;
+      const int* ver = I.Ver + r0d;
       int lo, hi;
       split(Ld, 4, p & 3, lo, hi);
       int mx = -8000;
@@ -1905,9 +1907,9 @@ struct Engine {
       for (int e = tid; e < NBP * R1; e += NT) {
         const int c = e / R1, r = e - c * R1;
         const bool ok = c < nb && rb + r < Ld;
-        cp8(sC + e, ok ? commit_col(cs.s_cid, c) + kp + rb + r : I.u, ok);
+        cp8(sC + e, ok ? commit_col(cs.s_cid, c) + r0d + rb + r : I.u, ok);
       }
-      if (tid < R1) cp4(sR + tid, rb + tid < Ld ? I.Ver + kp + rb + tid : I.Ver, rb + tid < Ld);
+      if (tid < R1) cp4(sR + tid, rb + tid < Ld ? I.Ver + r0d + rb + tid : I.Ver, rb + tid < Ld);
       cp_commit();
     };
     auto digits_c = [&](int b) {
@@ -2046,10 +2048,10 @@ struct Engine {
       const int t = o / nb, c = o - t * nb;
       double s = sL[((NLV - 1) * 32 + t) * NBP + c];
       for (int lam = NLV - 2; lam >= 0; --lam) s = fma(s, 0x1p-7, sL[(lam * 32 + t) * NBP + c]);
-      // rows t .. kp-1 of the triangle in FP64 (V(r, t) = 0 above row t)
+      // rows t .. r0d-1 in FP64 (V(r, t) = 0 above row t)
       const double* col = commit_col(cs.s_cid, c);
       double tri = 0.0;
-      for (int r = t; r < kp; ++r) tri = fma((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t], ldcg(col + r), tri);
+      for (int r = t; r < r0d; ++r) tri = fma((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t], ldcg(col + r), tri);
       cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14 + ebound(cs.s_vt[t])) + tri;  // 2^Ft: the reflector's scale
     }
     __syncthreads();
@@ -2079,7 +2081,7 @@ struct Engine {
       if (lane == 0) s_Ee[c] = ee;
     }
     __syncthreads();
-    // ---- pass 2 (digit rows kp .. L-1; the triangle rows after the loop)
+    // ---- pass 2 (digit rows r0d .. L-1; rows below r0d after the loop)
     const int nch2 = (Ld + R2 - 1) / R2;
     const bool act2 = warp < 8 * NTN;
     const int rt = warp & 7, nt2 = warp >> 3;
@@ -2100,7 +2102,7 @@ struct Engine {
       if (jc + 1 < nch2) stage_v(row2(jc + 1), R2, b ^ 1);
       if (act2) {
         // this thread's four elements: rows ra, ra + 8; columns c0, c0 + 1
-        const int ra = kp + rb + rt * 16 + g, rb8 = ra + 8;
+        const int ra = r0d + rb + rt * 16 + g, rb8 = ra + 8;
         double xv[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -2151,14 +2153,18 @@ struct Engine {
         }
       }
     }
-    // the triangle rows r < kp in FP64, in the order of the FP64 commit
-    // (they are not part of the trailing norm)
-    for (int o = tid; o < kp * nb; o += NT) {
+    // rows r < r0d in FP64, in the order of the FP64 commit; rows kp .. r0d-1
+    // belong to the trailing norm: kept for a fixed-order sum per column (in
+    // rows 8 .. 15 of s_nrm, which the row tiles below leave free)
+    double* s_tx = cs.s_nrm + 8 * CB;
+    for (int o = tid; o < r0d * nb; o += NT) {
       const int r = o / nb, c = o - r * nb;
       double* col = commit_col(cs.s_cid, c);
       double x = ldcg(col + r);
-      for (int t = 0; t <= r; ++t) x = fma(-((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t]), cs.s_E[t * CB + c], x);
+      for (int t = 0; t <= min(r, kp - 1); ++t)
+        x = fma(-((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t]), cs.s_E[t * CB + c], x);
       col[r] = x;
+      if (r >= kp) s_tx[(r - kp) * CB + c] = x;
     }
     // trailing norms: lanes of one column quad, then the 8 row tiles in order
 #pragma unroll
@@ -2174,6 +2180,7 @@ struct Engine {
     if (tid < nb) {
       double v = 0.0;
       for (int r8 = 0; r8 < 8; ++r8) v += cs.s_nrm[r8 * CB + tid];
+      for (int r = kp; r < r0d; ++r) v = fma(s_tx[(r - kp) * CB + tid], s_tx[(r - kp) * CB + tid], v);
       if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
     }
     return 0;
@@ -2332,7 +2339,7 @@ struct Engine {
     }
     const CommitShape cs{L, RC1, RC2, VS, wk, s_D, s_E, s_T, s_vt, s_nrm, s_cid};
     // the tensor-core form needs this panel's reflector digits
-    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 16384 && L >= kp + 64;  // int32 level sums
+    const bool tc = vd_ok && kp > 4 && kp <= 32 && L <= 16384 && L >= kp + 72;  // int32 level sums
     for (int base = 0; base < nl; base += CB) {
       const int nb = min(CB, nl - base);
       __syncthreads();

@@ -117,17 +117,19 @@ def reflector_scales(V, kp):
 def commit_digits(V, C, T, kp, guard=False):
     """The tensor-core commit restated; with guard=True pass 1's accuracy
     guard too (FP64 for the whole batch when it fires).  The digits cover
-    rows [kp, L); the reflectors' triangle (rows < kp: pivots and the zeros
-    above them) is summed in FP64.  Returns D, E, the updated C and the
-    number of batches sent to FP64 (0 or 1)."""
+    rows [r0d, L); the reflectors' triangle (rows < kp: pivots and the zeros
+    above them), rounded up to r0d = a multiple of 8 rows, is summed in
+    FP64.  Returns D, E, the updated C and the number of batches sent to FP64
+    (0 or 1)."""
     L, nb = V.shape[0], C.shape[1]
+    r0d = (kp + 7) & ~7
     Ft = reflector_scales(V, kp)
     Vs = np.array([[math.ldexp(V[r, t], -Ft[t]) for t in range(kp)] for r in range(L)])
     Er = [max(ebound(v) for v in Vs[r, :kp]) for r in range(L)]
-    a = [[digits(Vs[r, t], 56 - Er[r]) for t in range(kp)] for r in range(kp, L)]
-    Ec = [max([ebound(C[r, c]) + Er[r] for r in range(kp, L) if ebound(C[r, c]) > -2000] or [-8000])
+    a = [[digits(Vs[r, t], 56 - Er[r]) for t in range(kp)] for r in range(r0d, L)]
+    Ec = [max([ebound(C[r, c]) + Er[r] for r in range(r0d, L) if ebound(C[r, c]) > -2000] or [-8000])
           for c in range(nb)]
-    bC = [[digits(C[r, c], Er[r] + 56 - Ec[c]) for c in range(nb)] for r in range(kp, L)]
+    bC = [[digits(C[r, c], Er[r] + 56 - Ec[c]) for c in range(nb)] for r in range(r0d, L)]
     if guard and (guard_pass1(a, bC, kp, nb) < 2048).any():
         D = np.zeros((kp, nb))
         for t in range(kp):
@@ -148,12 +150,12 @@ def commit_digits(V, C, T, kp, guard=False):
     D = np.zeros((kp, nb))
     for t in range(kp):
         for c in range(nb):
-            lev = levels_pass1([a[i][t] for i in range(L - kp)], [bC[i][c] for i in range(L - kp)])
+            lev = levels_pass1([a[i][t] for i in range(L - r0d)], [bC[i][c] for i in range(L - r0d)])
             s = float(lev[ND])
             for lam in range(ND - 1, -1, -1):
                 s = s * 2.0 ** -7 + lev[lam]
             tri = 0.0
-            for r in range(t, kp):
+            for r in range(t, r0d):
                 tri = tri + V[r, t] * C[r, c]
             D[t, c] = math.ldexp(s, Ec[c] - 14 + Ft[t]) + tri
     E = T[:kp, :kp].T @ D
@@ -161,9 +163,10 @@ def commit_digits(V, C, T, kp, guard=False):
 
 
 def commit_pass2(V, C, E, kp):
-    """Pass 2, C - V E: rows [kp, L) from the digits of V / 2^Ft (row
-    scales) and of E'' = 2^Ft E (column scales), the triangle rows in FP64."""
+    """Pass 2, C - V E: rows [r0d, L) from the digits of V / 2^Ft (row
+    scales) and of E'' = 2^Ft E (column scales), the rows below r0d in FP64."""
     L, nb = C.shape
+    r0d = (kp + 7) & ~7
     Ft = reflector_scales(V, kp)
     Vs = np.array([[math.ldexp(V[r, t], -Ft[t]) for t in range(kp)] for r in range(L)])
     Er = [max(ebound(v) for v in Vs[r, :kp]) for r in range(L)]
@@ -174,9 +177,9 @@ def commit_pass2(V, C, E, kp):
     Cn = C.copy()
     for r in range(L):
         for c in range(nb):
-            if r < kp:
+            if r < r0d:
                 x = C[r, c]
-                for t in range(r + 1):
+                for t in range(min(r, kp - 1) + 1):
                     x = x - V[r, t] * E[t, c]
                 Cn[r, c] = x
                 continue
