@@ -1779,11 +1779,12 @@ struct Engine {
   // terms all lie far below the scale (a large entry of C paired with zeros
   // of V, say) loses bits that an FP64 dot product would keep.  Pass 1 also
   // forms the sum of |leading digit| products (one more MMA per step, exact
-  // integers), a lower bound of sum |v'||c'| in units of 2^(Ec - 14).  The
-  // digit result's error is at most 2L 2^(Ec-57) (times 2^Ft); where that
-  // could exceed the worst-case bound of the FP64 evaluation,
-  // gamma_L sum |v||c|, i.e. where the sum stays below 2^11, the batch goes
-  // to the FP64 commit before any column is touched.
+  // integers), a lower bound of sum |v'||c'| over the digit rows in units
+  // of 2^(Ec - 14).  The digit result's error is at most 2L 2^(Ec-57) (times
+  // 2^Ft); where that could exceed the worst-case bound of the FP64
+  // evaluation, gamma_L sum |v||c| - i.e. where the digit rows' sum plus the
+  // FP64 rows' sum |v||c| stays below 2^(Ec-3) (2^11 in the digits' units) -
+  // the batch goes to the FP64 commit before any column is touched.
   static constexpr float GUARD1 = 2048.0f;  // 2^11: sum |v'||c'| >= 2^(Ec-3)
   static constexpr unsigned ABS2 = 0x7FFF7FFFu;  // clears the signs of a bf16 pair
 
@@ -2015,21 +2016,17 @@ struct Engine {
       for (int j = 0; j < 4; ++j) sStage[((warp * NST + NST - 1) * 32 + lane) * 4 + j] = gacc[j];
     }
     __syncthreads();
-    // guard of pass 1: every (reflector, column) sum of |leading digit|
-    // products over the four row sub-blocks must reach GUARD1
+    // the guard's sums of |leading digit| products per (reflector, column),
+    // added over the four row sub-blocks (checked with D below)
+    float* sG = reinterpret_cast<float*>(reinterpret_cast<char*>(sV) + 32768);  // KM x CB
     for (int e = tid; e < COMBOS * 128; e += NT) {
       const int j = e & 3, ln = (e >> 2) & 31, cb = e >> 7;
       const int t = (cb % KT) * 16 + (ln >> 2) + ((j >> 1) << 3), c = (cb / KT) * 8 + 2 * (ln & 3) + (j & 1);
       if (t < kp && c < nb) {
         float g = 0.f;
         for (int sb = 0; sb < 4; ++sb) g += sStage[(((sb * COMBOS + cb) * NST + NST - 1) * 32 + ln) * 4 + j];
-        if (!(g >= GUARD1)) s_guard = 1;
+        sG[t * CB + c] = g;
       }
-    }
-    __syncthreads();
-    if (s_guard || I.guard_force == 1) {
-      if (tid == 0) atomicAdd(I.ctl + C_GUARD1, 1);
-      return 2;
     }
     for (int e = tid; e < COMBOS * NLV * 128; e += NT) {
       const int j = e & 3, ln = (e >> 2) & 31, lam = (e >> 7) % NLV, cb = (e >> 7) / NLV;
@@ -2048,13 +2045,27 @@ struct Engine {
       const int t = o / nb, c = o - t * nb;
       double s = sL[((NLV - 1) * 32 + t) * NBP + c];
       for (int lam = NLV - 2; lam >= 0; --lam) s = fma(s, 0x1p-7, sL[(lam * 32 + t) * NBP + c]);
-      // rows t .. r0d-1 in FP64 (V(r, t) = 0 above row t)
+      // rows t .. r0d-1 in FP64 (V(r, t) = 0 above row t), with sum |v||c|
       const double* col = commit_col(cs.s_cid, c);
-      double tri = 0.0;
-      for (int r = t; r < r0d; ++r) tri = fma((r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t], ldcg(col + r), tri);
-      cs.s_D[t * CB + c] = ldexp(s, s_Ec[c] - 14 + ebound(cs.s_vt[t])) + tri;  // 2^Ft: the reflector's scale
+      double tri = 0.0, tabs = 0.0;
+      for (int r = t; r < r0d; ++r) {
+        const double vr = (r > t) ? ldcg(I.V + (size_t)r * KM + t) : cs.s_vt[t], cr = ldcg(col + r);
+        tri = fma(vr, cr, tri);
+        tabs = fma(fabs(vr), fabs(cr), tabs);
+      }
+      const int es = s_Ec[c] + ebound(cs.s_vt[t]);  // 2^Ft: the reflector's scale
+      cs.s_D[t * CB + c] = ldexp(s, es - 14) + tri;
+      // guard: the digits' error (at most 2L 2^(es-57)) must stay within
+      // gamma_L sum |v||c|, whose lower bound is 2^(es-14) sG + tabs; a
+      // column without digit rows (all zero below r0d) has no digit error
+      if (s_Ec[c] > -8000 && !(ldexp((double)sG[t * CB + c], es - 14) + tabs >= ldexp((double)GUARD1, es - 14)))
+        s_guard = 1;
     }
     __syncthreads();
+    if (s_guard || I.guard_force == 1) {
+      if (tid == 0) atomicAdd(I.ctl + C_GUARD1, 1);
+      return 2;
+    }
     // D' = T^T D
     for (int o = tid; o < kp * nb; o += NT) {
       const int t = o % kp, cc = o / kp;

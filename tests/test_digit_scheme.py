@@ -130,7 +130,17 @@ def commit_digits(V, C, T, kp, guard=False):
     Ec = [max([ebound(C[r, c]) + Er[r] for r in range(r0d, L) if ebound(C[r, c]) > -2000] or [-8000])
           for c in range(nb)]
     bC = [[digits(C[r, c], Er[r] + 56 - Ec[c]) for c in range(nb)] for r in range(r0d, L)]
-    if guard and (guard_pass1(a, bC, kp, nb) < 2048).any():
+    fire = False
+    if guard:
+        S0 = guard_pass1(a, bC, kp, nb)
+        for t in range(kp):
+            for c in range(nb):
+                if Ec[c] == -8000:
+                    continue  # no digit rows: no digit error
+                tabs = sum(abs(V[r, t]) * abs(C[r, c]) for r in range(t, r0d))
+                es = Ec[c] + Ft[t]
+                fire |= not (math.ldexp(S0[t, c], es - 14) + tabs >= math.ldexp(2048.0, es - 14))
+    if fire:
         D = np.zeros((kp, nb))
         for t in range(kp):
             for c in range(nb):
@@ -352,3 +362,18 @@ def test_guard_is_quiet_on_ordinary_operands_long_panel():
     r1, r2, fb = bound_ratios(V, C, T, kp, guard=True)
     assert fb == 0
     assert r1 <= 1.0 and r2 <= 1.0
+
+
+def test_column_zero_below_the_triangle():
+    """A column that left the passive set re-enters with its trailing part
+    zero except at the top row (inside the FP64 rows): it has no digit rows,
+    so the guard does not send the batch to FP64, and both passes are exact
+    to FP64 rounding."""
+    rng = np.random.default_rng(9)
+    L, kp, nb = 40, 6, 3
+    V = triangular_V(rng, L, kp)
+    C = rng.standard_normal((L, nb))
+    C[1:, 1] = 0.0
+    T = np.triu(rng.standard_normal((kp, kp)))
+    r1, r2, fb = bound_ratios(V, C, T, kp, guard=True)
+    assert fb == 0 and r1 <= 1.0 and r2 <= 1.0
