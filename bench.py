@@ -31,6 +31,7 @@ METRIC = "NNLS solves/s: LHDM vs 1-col LH, same GB300, passive set exact, rel er
 WORKLOAD = ("overdetermined dense NNLS, A 4096x2048 U[0,1), 50% zero x, nonzeros U(0,1], "
             "b = A x + N(0,1e-4), seed 0, FP64")
 DFMA_PER_CLK_PER_SM = 2.0  # measured on this machine's GB300 (DFMA microbenchmark)
+MMA_SYNC_BF16_TFLOPS = 581.0  # mma.sync m16n8k16 bf16 with FP32 accumulation, measured on this machine's GB300
 
 
 def _oracle_solve(k_max):
@@ -160,21 +161,58 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def stored_traffic(workload_tag):
-    """DRAM bytes per launch of the solve kernel from the committed ncu
-    summary of this workload, if it was taken on the current sources."""
-    path = os.path.join(ROOT, "profiles", "lhdm_solve_grid_kernel_%s_ncu.md" % workload_tag)
+def stored_profile(workload_tag):
+    """The committed ncu summary (profiles/<kernel>_<workload>.json) of the
+    solve kernel on this workload, if it was taken on the current sources:
+    DRAM bytes per launch and the counters it lists; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "lhdm_solve_grid_kernel_%s.json" % workload_tag)
     try:
-        kv = {}
-        for line in open(path):
-            if ":" in line and line.startswith("- `"):
-                k, v = line[3:].split("`", 1)
-                kv[k] = v.split(":", 1)[1].strip()
-        if kv.get("sources_sha256") == kernel_sources_sha256():
-            return float(kv["dram_bytes_per_launch"])
+        prof = json.load(open(path))
+        if prof.get("sources_sha256") == kernel_sources_sha256():
+            return prof
     except Exception:
         pass
     return None
+
+
+def _oracle_batched(i):
+    """Spawned worker: one oracle solve of instance i of the batched workload
+    (k_max 16, the value the tuner picks for the mid-size buckets)."""
+    from oracle import oracle as O
+    from paper_2108_05345_gb300 import workloads as WL
+    m = WL.batched_sizes()[i]
+    A, b, _ = WL.batched_instance(i, m)
+    t0 = time.perf_counter()
+    O.nnls(A, b, k_max=16)
+    return time.perf_counter() - t0
+
+
+def _oracle_layer(i):
+    """Spawned worker: forward (oracle LHDM, k_max 32) and the closed-form
+    adjoint of instance i of the layer workload."""
+    import numpy as np
+    from oracle import oracle as O
+    from oracle.adjoint import nnls_adjoint
+    from paper_2108_05345_gb300 import workloads as WL
+    A, b, _, xt = WL.layer_batch(count=1, seed0=i)[0]
+    t0 = time.perf_counter()
+    r = O.nnls(A, b, k_max=32)
+    nnls_adjoint(A, b, r["x"], r["passive"], 2.0 * (r["x"] - xt))
+    return time.perf_counter() - t0
+
+
+def cpu_pool_baseline(fn, items, unit, what):
+    """fn over items on a spawned pool of every host core; solves/s of the
+    sample and the core count."""
+    cores = max(1, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(fn, items[:cores])  # warm the workers (imports, oracle build)
+        t0 = time.perf_counter()
+        secs = pool.map(fn, items)
+        wall = time.perf_counter() - t0
+    return {"value": len(items) / wall, "unit": unit, "cores": cores, "kind": "oracle",
+            "sample": "%s: %d instances on %d spawned workers, %.1f s wall, %.2f s per instance"
+                      % (what, len(items), cores, wall, sum(secs) / len(secs))}
 
 
 def batched_section(lhdm, WL, torch, np):
@@ -295,28 +333,141 @@ def layer_section(lhdm, WL, torch, np):
     }
 
 
-def sparse_section(lhdm, WL, torch, np, s=256):
-    """Sparse-recovery instance (A 2048x8192 Gaussian, unit-norm columns,
-    s nonzeros, noiseless): LHDM k_max = 64 vs one-column LH."""
-    A, b, x0 = WL.sparse_recovery_sweep(0, s)
+def _time_solve(ctx, lhdm, torch, At, bt, prm, reps=3, flush=None, **kw):
+    """Median CUDA-event time (ms) of `reps` solves (one warm-up first) and
+    the info of the last; kw selects solve_l1 (lam=...)."""
+    def run():
+        if "lam" in kw:
+            return ctx.solve_l1(At, bt, kw["lam"], prm, sync=False)
+        return ctx.solve(At, bt, prm, sync=False)
+    run()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = run()
+        c.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(c))
+    ts.sort()
+    return ts[len(ts) // 2], out, ctx.info()
+
+
+def kmax_section(lhdm, WL, torch, np, At, bt, ctx, flush):
+    """The 4096 x 2048 benchmark instance at k_max 16 and 64 (the headline
+    is k_max 32)."""
+    out = {}
+    for k in (16, 64):
+        ms, _, info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k), flush=flush)
+        out["k%d" % k] = {"ms": ms, "solves_per_s": 1000.0 / ms, "n_outer": int(info["n_outer"]),
+                          "n_passive": int(info["n_passive"])}
+    return out
+
+
+def small_section(lhdm, WL, torch, np):
+    """The 256 x 512 recovery instance (seed 0): LHDM k_max = 8 vs LH."""
+    A, b, x0 = WL.small_recovery(0)
     At = lhdm.colmajor(torch.from_numpy(A).cuda())
     bt = torch.from_numpy(b).cuda()
     ctx = lhdm.Context(*A.shape)
-    out = {"workload": "A 2048x8192 N(0,1) unit-norm columns, x0 %d nonzeros U(0.1,1], b = A x0, seed 0" % s}
-    for name, k in (("lhdm_k64", 64), ("lh", 1)):
-        prm = lhdm.default_params(k_max=k)
-        ctx.solve(At, bt, prm)
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        x, p, _ = ctx.solve(At, bt, prm, sync=False)
-        c.record()
-        torch.cuda.synchronize()
-        info = ctx.info()
+    out = {"workload": "A 256x512 N(0,1/256), x0 25 nonzeros U(0.1,1], b = A x0, seed 0 (L2-resident; no flush)"}
+    for name, k in (("lhdm_k8", 8), ("lh", 1)):
+        ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k), reps=10)
         xr = x.cpu().numpy()
-        out[name] = {"ms": a.elapsed_time(c), "n_outer": int(info["n_outer"]),
-                     "recovery_rel_err": float(np.linalg.norm(xr - x0) / np.linalg.norm(x0)),
-                     "support_exact": sorted(np.flatnonzero(xr > 0).tolist()) == sorted(np.flatnonzero(x0 > 0).tolist())}
-    out["speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k64"]["ms"]
+        out[name] = {"ms": ms, "solves_per_s": 1000.0 / ms, "n_outer": int(info["n_outer"]),
+                     "recovery_rel_err": float(np.linalg.norm(xr - x0) / np.linalg.norm(x0))}
+    out["speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k8"]["ms"]
+    ctx.close()
+    return out
+
+
+def sparse_section(lhdm, WL, torch, np):
+    """Sparse-recovery sweep (A 2048x8192 Gaussian, unit-norm columns,
+    s in {64, ..., 1024} nonzeros, noiseless): LHDM k_max = 64 vs LH,
+    time-to-solution and recovery per s."""
+    out = {"workload": "A 2048x8192 N(0,1) unit-norm columns, x0 s nonzeros U(0.1,1], b = A x0, seed 0"}
+    ctx = lhdm.Context(2048, 8192)
+    for s in (64, 128, 256, 512, 1024):
+        A, b, x0 = WL.sparse_recovery_sweep(0, s)
+        At = lhdm.colmajor(torch.from_numpy(A).cuda())
+        bt = torch.from_numpy(b).cuda()
+        row = {}
+        for name, k in (("lhdm_k64", 64), ("lh", 1)):
+            ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k), reps=1)
+            xr = x.cpu().numpy()
+            row[name] = {"ms": ms, "n_outer": int(info["n_outer"]), "n_passive": int(info["n_passive"]),
+                         "resid": float(info["resid_norm"]),
+                         "recovery_rel_err": float(np.linalg.norm(xr - x0) / np.linalg.norm(x0)),
+                         "support_exact": np.flatnonzero(xr > 1e-9 * xr.max()).tolist() == np.flatnonzero(x0).tolist()}
+        row["speedup_vs_lh"] = row["lh"]["ms"] / row["lhdm_k64"]["ms"]
+        out["s%d" % s] = row
+        del At, bt
+    ctx.close()
+    return out
+
+
+def signed_section(lhdm, WL, torch, np):
+    """Positivity trick (NNLS on [A -A] without forming -A): signed sparse
+    recovery with A 2048x8192 unit-norm Gaussian columns, s = 128 signed
+    nonzeros; LHDM k_max = 64 and LH, each with the inner loop and with the
+    sign flip."""
+    A, b, x0 = WL.signed_recovery(0, m=2048, n=8192, s=128, unit_columns=True)
+    At = lhdm.colmajor(torch.from_numpy(A).cuda())
+    bt = torch.from_numpy(b).cuda()
+    ctx = lhdm.Context(2048, 8192)
+    expect = np.concatenate([np.maximum(x0, 0), np.maximum(-x0, 0)])
+    out = {"workload": "[A -A], A 2048x8192 N(0,1) unit-norm columns, x0 128 signed nonzeros, b = A x0, seed 0"}
+    for name, k, mode in (("lhdm_k64", 64, 1), ("lhdm_k64_flip", 64, 2), ("lh", 1, 1), ("lh_flip", 1, 2)):
+        ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k, mode=mode), reps=1)
+        xr = x.cpu().numpy()
+        out[name] = {"ms": ms, "n_outer": int(info["n_outer"]), "n_inner": int(info["n_inner"]),
+                     "n_flip": int(info["n_flip"]),
+                     "recovery_rel_err": float(np.linalg.norm(xr - expect) / np.linalg.norm(expect))}
+    out["lh_flip_speedup_vs_lh"] = out["lh"]["ms"] / out["lh_flip"]["ms"]
+    out["lhdm_speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k64"]["ms"]
+    ctx.close()
+    return out
+
+
+def l1_section(lhdm, WL, torch, np):
+    """l1-NNLS (the stacked [1^T 1^T; lam A -lam A] system) on A 512x1024
+    with noisy signed sparse data, a sweep of lam."""
+    A, b0, x0 = WL.signed_recovery(0, m=512, n=1024, s=40)
+    b = b0 + 1e-3 * np.random.default_rng(5).normal(size=512)
+    At = lhdm.colmajor(torch.from_numpy(A).cuda())
+    bt = torch.from_numpy(b).cuda()
+    ctx = lhdm.Context(513, 2048)
+    out = {"workload": "l1-NNLS, A 512x1024 N(0,1/512), x0 40 signed nonzeros, b = A x0 + 1e-3 N(0,1), seed 0",
+           "k_max": 32, "sweep": {}}
+    total = 0.0
+    for lam in (1.0, 10.0, 100.0):
+        ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=32), reps=3, lam=lam)
+        xr = x.cpu().numpy()
+        xs = xr[:1024] - xr[1024:]
+        total += ms
+        out["sweep"]["lam=%g" % lam] = {"ms": ms, "n_outer": int(info["n_outer"]), "n_passive": int(info["n_passive"]),
+                                        "l1": float(np.abs(xs).sum()),
+                                        "dist_to_x0": float(np.linalg.norm(xs - x0) / np.linalg.norm(x0))}
+    out["sweep_ms"] = total
+    ctx.close()
+    return out
+
+
+def conditioned_section(lhdm, WL, torch, np):
+    """Ill-conditioned dense NNLS (condition number ~1e6): A 2048x1024,
+    LHDM k_max = 32 vs LH."""
+    A, b, _ = WL.conditioned_overdetermined(0, kappa=1e6)
+    At = lhdm.colmajor(torch.from_numpy(A).cuda())
+    bt = torch.from_numpy(b).cuda()
+    ctx = lhdm.Context(*A.shape)
+    out = {"workload": "A 2048x1024 = U diag(sigma) V^T, sigma 1..1e-6 log-spaced, unit-norm columns, "
+                       "50% zero x, b = A x + N(0,1e-4), seed 0"}
+    for name, k in (("lhdm_k32", 32), ("lh", 1)):
+        ms, _, info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k), reps=1)
+        out[name] = {"ms": ms, "n_outer": int(info["n_outer"]), "n_passive": int(info["n_passive"])}
+    out["speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k32"]["ms"]
     ctx.close()
     return out
 
@@ -399,7 +550,7 @@ def main():
     barrier()
     clocks = clk.stop()
     x, p, info = ctx.solve(At, bt, prm)
-    ms_ph, fl_ph = ctx.profile()
+    ms_ph, fl_ph, n_mma = ctx.profile_full()
     trace = ctx.trace()
     ms = float(np.mean(t_lhdm))
     if world > 1:
@@ -448,6 +599,21 @@ def main():
     achieved = flops_total / (kernel_ms * 1e-3) / 1e12
     nZ_bytes = fl_ph["dual"] / 2.0 * 8.0 if fl_ph["dual"] else 0.0  # 8 bytes of A per FMA
     dual_gbs = nZ_bytes / (ms_ph["dual"] * 1e-3) / 1e9 if ms_ph["dual"] > 0 else None
+    # the units that bind the solve, each against its own peak:
+    #  - streaming A: 8 m n per outer step plus 8 m nP for the residual
+    #    (the per-solve bytes of the method's BLAS-2 part), over the solve time;
+    #  - the FP64 pipe: the algorithmic FP64 flops of every phase but the
+    #    tensor-core commit, over the time of those phases;
+    #  - the tensor pipe: the commit's bf16 MMAs (m16n8k16, 4096 flops),
+    #    over the commit time, against the mma.sync bf16 rate measured on this
+    #    pool's GB300 (the cuBLAS figure of MEASURED_PEAKS is tcgen05)
+    sum_np = float(trace[:, 3].sum()) if len(trace) else 0.0
+    bytes_stream = 8.0 * m * n * info["n_outer"] + 8.0 * m * sum_np
+    stream_gbs = bytes_stream / (kernel_ms * 1e-3) / 1e9
+    fp64_ms = sum(v for k, v in ms_ph.items() if k != "commit")
+    fp64_flops = sum(v for k, v in fl_ph.items() if k != "commit")
+    mma_tflops = n_mma * 4096.0 / (ms_ph["commit"] * 1e-3) / 1e12 if ms_ph["commit"] > 0 else 0.0
+    prof = stored_profile("4096x2048")
 
     # parity against the CPU oracle (same instance, same parameters)
     x_np, p_np = x.cpu().numpy(), p.cpu().numpy()
@@ -484,8 +650,25 @@ def main():
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "peak_source": "derived: %.0f DFMA/clk/SM (measured) x %d SMs x %.0f MHz"
                                     % (DFMA_PER_CLK_PER_SM, nsm, sm_mhz_peak),
-                     "algorithmic_flops": flops_total, "traffic": stored_traffic("4096x2048"),
-                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/; null if the sources changed since)"},
+                     "algorithmic_flops": flops_total,
+                     "achieved_meaning": "FP64-equivalent: the commit's share runs on the bf16 tensor cores",
+                     "traffic": prof["dram_bytes_per_launch"] if prof else None,
+                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/*.json; null if the sources changed since)",
+                     "units": {
+                         "hbm_stream_A": {"achieved": stream_gbs, "peak": hbm, "unit": "GB/s",
+                                          "frac": stream_gbs / hbm, "peak_source": hbm_src,
+                                          "bytes": bytes_stream,
+                                          "bytes_formula": "8 m n N_outer + 8 m sum_steps nP"},
+                         "fp64_pipe": {"achieved": fp64_flops / (fp64_ms * 1e-3) / 1e12 if fp64_ms > 0 else None,
+                                       "peak": fp64_peak, "unit": "TFLOP/s",
+                                       "frac": (fp64_flops / (fp64_ms * 1e-3) / 1e12) / fp64_peak if fp64_ms > 0 else None,
+                                       "scope": "all phases but the commit, over their time"},
+                         "tensor_pipe": {"achieved": mma_tflops, "peak": MMA_SYNC_BF16_TFLOPS, "unit": "TFLOP/s",
+                                         "frac": mma_tflops / MMA_SYNC_BF16_TFLOPS, "mma_instructions": n_mma,
+                                         "scope": "the commit's bf16 mma.sync digit products over the commit time",
+                                         "peak_source": "measured mma.sync m16n8k16 bf16 rate on this pool's GB300"},
+                     },
+                     "ncu": {k: prof[k] for k in prof if k not in ("sources_sha256",)} if prof else None},
         "dual_gemv": {"achieved_gbs": dual_gbs, "hbm_peak_gbs": hbm, "hbm_source": hbm_src,
                       "frac_of_hbm": (dual_gbs / hbm) if dual_gbs else None,
                       "fp64_frac": ((fl_ph["dual"] / (ms_ph["dual"] * 1e-3) / 1e12) / fp64_peak) if ms_ph["dual"] else None},
@@ -497,9 +680,22 @@ def main():
         "clocks": clocks,
     }
     if not args.no_extra and world == 1:
+        line["kmax"] = kmax_section(lhdm, WL, torch, np, At, bt, ctx, flush)
+        line["small"] = small_section(lhdm, WL, torch, np)
         line["batched"] = batched_section(lhdm, WL, torch, np)
         line["layer"] = layer_section(lhdm, WL, torch, np)
         line["sparse_recovery"] = sparse_section(lhdm, WL, torch, np)
+        line["signed"] = signed_section(lhdm, WL, torch, np)
+        line["l1"] = l1_section(lhdm, WL, torch, np)
+        line["conditioned"] = conditioned_section(lhdm, WL, torch, np)
+        if not args.no_cpu:
+            sizes = WL.batched_sizes()
+            line["batched"]["cpu_baseline"] = cpu_pool_baseline(
+                _oracle_batched, list(range(0, 1024, 8)), "solves/s",
+                "oracle LHDM (k_max 16) of every 8th batched instance")
+            line["layer"]["cpu_baseline"] = cpu_pool_baseline(
+                _oracle_layer, list(range(0, 256, 4)), "solves/s",
+                "oracle LHDM (k_max 32) forward + closed-form adjoint of every 4th layer instance")
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -346,8 +346,10 @@ int lhdm_debug_state(lhdm_ctx* ctx, const char* name, void* host, int64_t count,
  * inner-loop control and bookkeeping, residual, dual vector, feasibility
  * loop, Givens chain on R, rotations of the Z columns, triangular solves of
  * the inner loop; ms[12..24) = the algorithmic FP64 flops of the same
- * phases (an FMA counts 2).  Writes min(n, 24) values and returns how many
- * (negative status on error).  Synchronises the stream. */
+ * phases (an FMA counts 2); ms[24] = bf16 tensor-core MMA instructions
+ * (m16n8k16, 4096 flops each) the commit issued.  Writes min(n, 25) values
+ * and returns how many (negative status on error).  Synchronises the
+ * stream. */
 int lhdm_phase_times(lhdm_ctx* ctx, double* ms, int32_t n, void* stream);
 
 /*

@@ -199,8 +199,8 @@ int lhdm_create(lhdm_ctx** out, int32_t max_m, int32_t max_n, int32_t max_batch)
   if (e == cudaSuccess) e = cudaMalloc(&c->bar, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_info, sizeof(lhdm_info));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_phase, 2 * NPHASE * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 2 * NPHASE * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_phase, (2 * NPHASE + 2) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, (2 * NPHASE + 2) * sizeof(double));
   c->trace_cap = 3 * max_n + 8;
   if (e == cudaSuccess) e = cudaMalloc(&c->d_trace, (size_t)6 * c->trace_cap * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_zero, sizeof(int));
@@ -342,12 +342,12 @@ int lhdm_get_info(lhdm_ctx* c, lhdm_info* info, void* stream) {
 int lhdm_phase_times(lhdm_ctx* c, double* ms, int32_t n, void* stream) {
   static_assert(NPHASE == 12, "phase list documented in lhdm.h");
   if (!c || !ms || n < 0) return -LHDM_ERR_INVALID_ARG;
-  double h[2 * NPHASE];
+  double h[2 * NPHASE + 1];
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(h, c->d_phase, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return -LHDM_ERR_CUDA;
-  const int k = std::min<int>(n, 2 * NPHASE);
+  const int k = std::min<int>(n, 2 * NPHASE + 1);
   for (int i = 0; i < k; ++i) ms[i] = (i < NPHASE) ? h[i] * 1e-6 : h[i];
   return k;
 }

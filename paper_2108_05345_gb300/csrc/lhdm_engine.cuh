@@ -122,7 +122,8 @@ struct Inst {
   unsigned* Vd;   // panel reflectors as 7-bit digits: m rows x ND planes x 16 words (bf16 pairs,
                   // 16-byte chunk c of row r at c ^ (r & 7)), null: none
   int* Ver;       // m: row scale exponents of Vd (|V(r, :)| < 2^Ver[r])
-  double* phase_ns;           // NPHASE (may be null)
+  double* phase_ns;           // 2 NPHASE + 1 (may be null): phase times, phase flops,
+                              // bf16 MMAs of the tensor-core commit
   int* trace;                 // 6 ints per outer step (may be null)
   int trace_cap;              // rows available in trace
   long long wait_ns;          // bound on a wait for another CTA (ns)

@@ -159,6 +159,7 @@ struct Engine {
       I.order[p] = -1;
     }
     if (tm.rank == 0 && tid < 16) I.ctl[tid] = 0;
+    if (tm.rank == 0 && tid == 0 && I.phase_ns) I.phase_ns[2 * NPHASE] = 0.0;  // MMA count
     clear_tri_flags();
     am = block_max(am, sh);
     bs = block_sum(bs, sh);
@@ -2062,8 +2063,14 @@ struct Engine {
         s_guard = 1;
     }
     __syncthreads();
+    // bf16 MMAs of pass 1: per chunk, each MMA warp's 16 rows take the 43
+    // digit pairs and the guard's
+    const double mma1 = (double)MW * nch1 * 44.0;
     if (s_guard || I.guard_force == 1) {
-      if (tid == 0) atomicAdd(I.ctl + C_GUARD1, 1);
+      if (tid == 0) {
+        atomicAdd(I.ctl + C_GUARD1, 1);
+        if (I.phase_ns) atomicAdd(I.phase_ns + 2 * NPHASE, mma1);
+      }
       return 2;
     }
     // D' = T^T D
@@ -2194,6 +2201,8 @@ struct Engine {
       for (int r = kp; r < r0d; ++r) v = fma(s_tx[(r - kp) * CB + tid], s_tx[(r - kp) * CB + tid], v);
       if (cs.s_cid[tid] >= 0) I.u[cs.s_cid[tid]] = sqrt(v);
     }
+    if (tid == 0 && I.phase_ns)  // pass 2: 43 digit pairs per 16 x 8 tile and 16 reflectors
+      atomicAdd(I.phase_ns + 2 * NPHASE, mma1 + (double)(8 * NTN) * nch2 * KT * 43.0);
     return 0;
   }
 

@@ -366,14 +366,20 @@ class Context:
 
     def profile(self, stream=None):
         """({phase: ms}, {phase: algorithmic FP64 flops}) of the last solve."""
-        n = 2 * len(PHASES)
+        ms, fl, _ = self.profile_full(stream)
+        return ms, fl
+
+    def profile_full(self, stream=None):
+        """({phase: ms}, {phase: algorithmic FP64 flops}, bf16 MMA
+        instructions of the tensor-core commit) of the last solve."""
+        n = 2 * len(PHASES) + 1
         buf = (C.c_double * n)()
         k = lib().lhdm_phase_times(self.h, buf, n, _stream(stream))
         if k < n:
             raise RuntimeError("lhdm_phase_times failed")
         ms = {PHASES[i]: buf[i] for i in range(len(PHASES))}
         fl = {PHASES[i]: buf[len(PHASES) + i] for i in range(len(PHASES))}
-        return ms, fl
+        return ms, fl, buf[2 * len(PHASES)]
 
 
 class Batch:
