@@ -205,11 +205,23 @@ def cpu_pool_baseline(fn, items, unit, what):
     """fn over items on a spawned pool of every host core; solves/s of the
     sample and the core count."""
     cores = max(1, os.cpu_count() or 1)
-    with mp.get_context("spawn").Pool(cores) as pool:
-        pool.map(fn, items[:cores])  # warm the workers (imports, oracle build)
-        t0 = time.perf_counter()
-        secs = pool.map(fn, items)
-        wall = time.perf_counter() - t0
+    # one thread per worker: numpy's BLAS would otherwise start a thread per
+    # core in every worker
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(fn, items[:cores])  # warm the workers (imports, oracle build)
+            t0 = time.perf_counter()
+            secs = pool.map(fn, items)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return {"value": len(items) / wall, "unit": unit, "cores": cores, "kind": "oracle",
             "sample": "%s: %d instances on %d spawned workers, %.1f s wall, %.2f s per instance"
                       % (what, len(items), cores, wall, sum(secs) / len(secs))}
@@ -409,25 +421,37 @@ def sparse_section(lhdm, WL, torch, np):
 
 
 def signed_section(lhdm, WL, torch, np):
-    """Positivity trick (NNLS on [A -A] without forming -A): signed sparse
-    recovery with A 2048x8192 unit-norm Gaussian columns, s = 128 signed
-    nonzeros; LHDM k_max = 64 and LH, each with the inner loop and with the
-    sign flip."""
-    A, b, x0 = WL.signed_recovery(0, m=2048, n=8192, s=128, unit_columns=True)
-    At = lhdm.colmajor(torch.from_numpy(A).cuda())
-    bt = torch.from_numpy(b).cuda()
-    ctx = lhdm.Context(2048, 8192)
-    expect = np.concatenate([np.maximum(x0, 0), np.maximum(-x0, 0)])
-    out = {"workload": "[A -A], A 2048x8192 N(0,1) unit-norm columns, x0 128 signed nonzeros, b = A x0, seed 0"}
-    for name, k, mode in (("lhdm_k64", 64, 1), ("lhdm_k64_flip", 64, 2), ("lh", 1, 1), ("lh_flip", 1, 2)):
-        ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k, mode=mode), reps=1)
-        xr = x.cpu().numpy()
-        out[name] = {"ms": ms, "n_outer": int(info["n_outer"]), "n_inner": int(info["n_inner"]),
-                     "n_flip": int(info["n_flip"]),
-                     "recovery_rel_err": float(np.linalg.norm(xr - expect) / np.linalg.norm(expect))}
-    out["lh_flip_speedup_vs_lh"] = out["lh"]["ms"] / out["lh_flip"]["ms"]
-    out["lhdm_speedup_vs_lh"] = out["lh"]["ms"] / out["lhdm_k64"]["ms"]
-    ctx.close()
+    """Positivity trick (NNLS on [A -A] without forming -A), LHDM k_max and
+    LH, each with the inner loop and with the sign flip: signed sparse
+    recovery (A 2048x8192 unit-norm Gaussian columns, s = 128 signed
+    nonzeros, noiseless; no negative y arises) and signed least squares
+    (A 2048x1024 Gaussian, x ~ N(0,1), b = A x + N(0,1): the inner loop and
+    the sign flip both run)."""
+    out = {}
+    cases = (("recovery", WL.signed_recovery(0, m=2048, n=8192, s=128, unit_columns=True), 64,
+              "[A -A], A 2048x8192 N(0,1) unit-norm columns, x0 128 signed nonzeros, b = A x0, seed 0"),
+             ("least_squares", WL.signed_overdetermined(0, m=2048, n=1024, noise_var=1.0), 32,
+              "[A -A], A 2048x1024 N(0,1/2048), x ~ N(0,1), b = A x + N(0,1), seed 0"))
+    for tag, (A, b, x0), k_dm, desc in cases:
+        At = lhdm.colmajor(torch.from_numpy(A).cuda())
+        bt = torch.from_numpy(b).cuda()
+        ctx = lhdm.Context(*A.shape)
+        row = {"workload": desc}
+        for name, k, mode in (("lhdm_k%d" % k_dm, k_dm, 1), ("lhdm_k%d_flip" % k_dm, k_dm, 2), ("lh", 1, 1),
+                              ("lh_flip", 1, 2)):
+            ms, (x, p, _), info = _time_solve(ctx, lhdm, torch, At, bt, lhdm.default_params(k_max=k, mode=mode), reps=1)
+            xr = x.cpu().numpy()
+            n = A.shape[1]
+            r = {"ms": ms, "n_outer": int(info["n_outer"]), "n_inner": int(info["n_inner"]),
+                 "n_flip": int(info["n_flip"]), "resid": float(info["resid_norm"])}
+            if tag == "recovery":
+                expect = np.concatenate([np.maximum(x0, 0), np.maximum(-x0, 0)])
+                r["recovery_rel_err"] = float(np.linalg.norm(xr - expect) / np.linalg.norm(expect))
+            row[name] = r
+        row["lh_flip_speedup_vs_lh"] = row["lh"]["ms"] / row["lh_flip"]["ms"]
+        row["lhdm_speedup_vs_lh"] = row["lh"]["ms"] / row["lhdm_k%d" % k_dm]["ms"]
+        out[tag] = row
+        ctx.close()
     return out
 
 
