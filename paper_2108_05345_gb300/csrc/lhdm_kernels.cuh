@@ -41,7 +41,7 @@ struct ScratchLayout {
   size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, candw, rotc, rots, apu;
   size_t Dinv, accb;  // pipelined triangular solve (teams of more than one CTA)
   size_t dtotal;
-  size_t Vd;  // reflector digits (teams of more than one CTA)
+  size_t Vd;  // reflector digits of the tensor-core commit
   size_t pos, J, candi, candn, ipart, ctl, qlist, tflag, Ver, csign;
   size_t itotal;
   int ldw;
@@ -82,7 +82,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.pipelined = team > 1;
   L.Dinv = take(L.pipelined ? nbk * TB * TB : 1);
   L.accb = take(L.pipelined ? nbk * TB : 1);
-  L.Vd = take(L.pipelined ? (size_t)ND * m * 8 : 1);  // m x ND x 16 words
+  L.Vd = take((size_t)ND * m * 8);  // m x ND x 16 words
   L.dtotal = o;
   o = 0;
   L.pos = take(n);
@@ -93,7 +93,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.ctl = take(16);
   L.qlist = take(cap);
   L.tflag = take(L.pipelined ? nbk * (1 + TB / SLAB + INV_PARTS) : 1);
-  L.Ver = take(L.pipelined ? m : 1);
+  L.Ver = take(m);
   L.csign = take(n);
   L.itotal = o;
   return L;
@@ -131,8 +131,8 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.Dinv = L.pipelined ? d + L.Dinv : nullptr;
   I.accb = L.pipelined ? d + L.accb : nullptr;
   I.tflag = L.pipelined ? ip + L.tflag : nullptr;
-  I.Vd = L.pipelined ? reinterpret_cast<unsigned*>(d + L.Vd) : nullptr;
-  I.Ver = L.pipelined ? ip + L.Ver : nullptr;
+  I.Vd = reinterpret_cast<unsigned*>(d + L.Vd);
+  I.Ver = ip + L.Ver;
   I.amask = nullptr;
   I.wait_ns = WAIT_NS;
   I.bar_extra = 0;

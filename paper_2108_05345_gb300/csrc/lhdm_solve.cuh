@@ -610,7 +610,48 @@ struct Engine {
       __syncthreads();
     }
     kk = i;  // reflectors formed (truncated by the rank bound)
+    if constexpr (std::is_same<Team, CtaTeam>::value) {
+      // a one-CTA team holds every row: the digits of the tensor-core commit
+      if (I.Vd != nullptr && kk > 4 && kk <= 32) {
+        __syncthreads();
+        for (int rr = warp; rr < L; rr += NW) {
+          const double v0 = (lane < kk) ? ldcg(I.vtop + lane) : 1.0;
+          const double vr = (lane < kk) ? (rr > lane ? ldcg(V + (size_t)rr * KM + lane) : (rr == lane ? v0 : 0.0)) : 0.0;
+          vd_store_row(rr, vr, v0);
+        }
+        vd_ok = true;
+      }
+    }
     return sync();
+  }
+
+  // One row of the panel's reflectors as 7-bit digits for the tensor-core
+  // commit (one warp; lane t holds V(row, t) - v0 on the diagonal, zero
+  // above - and v0 of reflector t).  Reflector t is scaled by 2^-Ft,
+  // 2^Ft > |v0| >= |V(:, t)|; the row scale is the largest exponent bound of
+  // the scaled row, and even lanes store digit pairs.
+  __device__ __forceinline__ void vd_store_row(int row, double vrow, double v0) {
+    const double v = scale2(vrow, -ebound(v0));
+    const int er = __reduce_max_sync(0xffffffffu, ebound(v));
+    unsigned ha, la;
+    halves28(fix56(v, 56 - er), ha, la);
+    const unsigned hb = __shfl_down_sync(0xffffffffu, ha, 1), lb = __shfl_down_sync(0xffffffffu, la, 1);
+    const bool nega = v < 0.0;
+    const bool negb = __shfl_down_sync(0xffffffffu, nega ? 1 : 0, 1) != 0;
+    unsigned sg, nb2;
+    sign2(nega, negb, sg, nb2);
+    if ((lane & 1) == 0) {
+      // a row holds its ND digit planes (16 words each) side by side;
+      // 16-byte chunk c of the row is stored at c ^ (row & 7), as the
+      // commit's shared-memory layout expects
+      const int w = lane >> 1;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        const int c = (4 * k + (w >> 2)) ^ (row & 7);
+        I.Vd[(size_t)row * (16 * ND) + c * 4 + (w & 3)] = dig2k(k, ha, la, hb, lb, sg, nb2);
+      }
+    }
+    if (lane == 0) I.Ver[row] = er;
   }
 
   // Panel with the team's rows held in shared memory (at most PR_MAX rows
@@ -981,36 +1022,12 @@ struct Engine {
       const int rr = e / kk, t = e - rr * kk;
       I.V[(size_t)(q0 + rr) * KM + t] = sP[rr * PS + t];
     }
-    // the same rows as 7-bit digits for the tensor-core commit: one warp per
-    // row, lane t holds V(row, t) (v0 on the diagonal, zero above), the row
-    // scale is its largest exponent bound, and even lanes store digit pairs
+    // the same rows as 7-bit digits for the tensor-core commit
     if (I.Vd != nullptr && kk > 4 && kk <= 32) {
       for (int rr = warp; rr < nr; rr += NW) {
         const int row = q0 + rr;
-        // reflector lane scaled by 2^-Ft, 2^Ft > |v0| >= |V(:, lane)|
-        const double v = (lane < kk) ? scale2(row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0),
-                                              -ebound(s_v0[lane]))
-                                     : 0.0;
-        const int er = __reduce_max_sync(0xffffffffu, ebound(v));
-        unsigned ha, la;
-        halves28(fix56(v, 56 - er), ha, la);
-        const unsigned hb = __shfl_down_sync(0xffffffffu, ha, 1), lb = __shfl_down_sync(0xffffffffu, la, 1);
-        const bool nega = v < 0.0;
-        const bool negb = __shfl_down_sync(0xffffffffu, nega ? 1 : 0, 1) != 0;
-        unsigned sg, nb2;
-        sign2(nega, negb, sg, nb2);
-        if ((lane & 1) == 0) {
-          // a row holds its ND digit planes (16 words each) side by side;
-          // 16-byte chunk c of the row is stored at c ^ (row & 7), as the
-          // commit's shared-memory layout expects
-          const int w = lane >> 1;
-#pragma unroll
-          for (int k = 0; k < ND; ++k) {
-            const int c = (4 * k + (w >> 2)) ^ (row & 7);
-            I.Vd[(size_t)row * (16 * ND) + c * 4 + (w & 3)] = dig2k(k, ha, la, hb, lb, sg, nb2);
-          }
-        }
-        if (lane == 0) I.Ver[row] = er;
+        vd_store_row(row, (lane < kk) ? (row > lane ? sP[rr * PS + lane] : (row == lane ? s_v0[lane] : 0.0)) : 0.0,
+                     (lane < kk) ? s_v0[lane] : 1.0);
       }
     }
     if (tm.rank == 0) {
@@ -2365,15 +2382,13 @@ struct Engine {
       __syncthreads();
       if (tid < nb) s_cid[tid] = s_list[base + tid];
       __syncthreads();
-      if constexpr (std::is_same<Team, GridTeam>::value) {  // only whole-grid teams have digits
-        if (tc) {
-          int r;
-          if (kp <= 16) r = (nb <= 8) ? commit_tc<8, 1>(cs, nb) : commit_tc<16, 1>(cs, nb);
-          else r = (nb <= 8) ? commit_tc<8, 2>(cs, nb) : commit_tc<16, 2>(cs, nb);
-          if (r == 1) return false;
-          if (r == 0) continue;
-          __syncthreads();  // r == 2: the FP64 commit below takes this batch
-        }
+      if (tc) {
+        int r;
+        if (kp <= 16) r = (nb <= 8) ? commit_tc<8, 1>(cs, nb) : commit_tc<16, 1>(cs, nb);
+        else r = (nb <= 8) ? commit_tc<8, 2>(cs, nb) : commit_tc<16, 2>(cs, nb);
+        if (r == 1) return false;
+        if (r == 0) continue;
+        __syncthreads();  // r == 2: the FP64 commit below takes this batch
       }
       switch (nb) {
         case 1: commit_batch<1>(cs); break;
