@@ -54,6 +54,8 @@ constexpr int TB = 64;               // triangular-solve block
 constexpr int SLAB = 16;             // rows per accumulation slab of the pipelined solve
 constexpr int INV_PARTS = TB / NW;   // column classes of a diagonal-block inverse (one column per warp)
 constexpr int DB = 32;               // downdate block (positions per warp)
+constexpr int PACC_COPIES = 4;       // copies of the panel exchange's sums (ranks mod 4)
+constexpr int PACC_W = PACC_COPIES * 2 * (KM + 1);  // one exchange buffer (int64 words)
 constexpr int NPHASE = 12;
 constexpr double EPS = 2.220446049250313e-16;  // 2^-52
 constexpr long long WAIT_NS = 4000000000LL;    // default bound on any device-side wait
@@ -103,6 +105,7 @@ struct Inst {
   double* yJ;     // KM
   double* pr;     // KM (panel right-hand side)
   double* part;   // team.size x PW
+  long long* pacc;  // 3 x PACC_W: fixed-point sums of the panel exchange
   double* candw;  // team.size x KM
   double* rotc;   // rotation log
   double* rots;
@@ -366,6 +369,12 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (x * pow2n(e1)) * pow2n(e - e1);
 }
 
+// x with |x| <= 2^(E-1) as a fixed-point integer in units of 2^(E-56)
+// (truncated; |q| <= 2^55).  Such integers add exactly and in any order to
+// the same sum, and up to 256 of them fit in 64 bits.
+__device__ __forceinline__ long long fx_q(double x, int E) { return __double2ll_rz(scale2(x, 56 - E)); }
+__device__ __forceinline__ double fx_x(long long q, int E) { return scale2((double)q, E - 56); }
+
 // ---------------------------------------------------------------- teams
 // Whole-grid team: one CTA per SM, co-resident (cooperative launch).  The
 // barrier is a generation counter; every wait is bounded by wait_ns and sets
@@ -375,41 +384,54 @@ __device__ __forceinline__ double scale2(double x, int e) {
 // every wait runs out.
 struct GridTeam {
   int rank, size;
-  unsigned int* bar;  // [0] arrivals, [1] generation; [2], [3] the same for sub-teams
+  // [0] arrivals at whole-team barriers, [2] arrivals at sub-team barriers
+  // (both zero at launch; [2] is zeroed again after every panel): the k-th
+  // barrier completes when its counter reaches the arrivals of barriers
+  // 1..k, so an arrival is one release-add and nothing is ever reset
+  // inside a barrier
+  unsigned int* bar;
   int* err;
   long long wait_ns;
-  int extra;
-  __device__ __forceinline__ bool sync() { return sync_words(bar, size + extra); }
+  int extra;  // arrivals a whole-team barrier expects beyond the team
+  unsigned int full_target = 0u, sub_target = 0u;
+  __device__ __forceinline__ bool sync() {
+    full_target += (unsigned)(size + extra);
+    return arrive_wait(bar, full_target);
+  }
   // barrier of ranks 0 .. n-1 only (the other ranks must not call it)
-  __device__ __forceinline__ bool sync_sub(int n) { return sync_words(bar + 2, n); }
-  __device__ __forceinline__ bool sync_words(unsigned int* bw, int n) {
+  __device__ __forceinline__ bool sync_sub(int n) {
+    sub_target += (unsigned)n;
+    return arrive_wait(bar + 2, sub_target);
+  }
+  // after a whole-team barrier that follows the last sub-team barrier of a
+  // panel (every rank calls it): the sub-team count starts again from zero
+  __device__ __forceinline__ void sub_reset() {
+    if (rank == 0 && threadIdx.x == 0) atomicExch(bar + 2, 0u);
+    sub_target = 0u;
+  }
+  __device__ __forceinline__ bool arrive_wait(unsigned int* cnt, unsigned int target) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-      // the CTA barrier orders every thread's writes before this fence,
-      // which is cumulative: one fence per CTA publishes them
-      __threadfence();
       int ok = 1;
-      volatile unsigned int* gen = bw + 1;
-      const unsigned int g = *gen;
-      __threadfence();
-      const unsigned int prev = atomicAdd(bw, 1u);
-      if (prev == (unsigned int)n - 1u) {
-        atomicExch(bw, 0u);
-        __threadfence();
-        atomicAdd(bw + 1, 1u);
-      } else {
-        const long long t0 = gtimer();
-        unsigned int spins = 0;
-        while (*gen == g) {
-          if ((++spins & 63u) == 0u) {
-            if (*(volatile int*)err) { ok = 0; break; }
-            if (gtimer() - t0 > wait_ns) { atomicExch(err, 1); ok = 0; break; }
-          }
+      // release: what the CTA wrote before the CTA barrier above is visible
+      // to every CTA that acquires a count including this arrival
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
+      const long long t0 = gtimer();
+      unsigned int spins = 0;
+      for (;;) {
+        // err first (relaxed), so that both loads are in flight together
+        const int e = *(volatile int*)err;
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+        if (e) { ok = 0; break; }
+        if (v >= target) break;
+        if ((++spins & 63u) == 0u && gtimer() - t0 > wait_ns) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
-      if (*(volatile int*)err) ok = 0;
       s_ok = ok;
     }
     __syncthreads();
@@ -426,6 +448,7 @@ struct CtaTeam {
     return true;
   }
   __device__ __forceinline__ bool sync_sub(int) { return sync(); }
+  __device__ __forceinline__ void sub_reset() {}
 };
 
 // Bounded wait until *flag >= target (one thread); false on timeout.

@@ -38,7 +38,7 @@ struct BatchItem {
 
 // Offsets of one team's scratch inside a double region and an int region.
 struct ScratchLayout {
-  size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, candw, rotc, rots, apu;
+  size_t W, bt, yP, rhs, w, u, anorm, V, vtop, beta, T, R22, Gm, yJ, pr, part, pacc, candw, rotc, rots, apu;
   size_t Dinv, accb;  // pipelined triangular solve (teams of more than one CTA)
   size_t dtotal;
   size_t Vd;  // reflector digits of the tensor-core commit
@@ -73,6 +73,7 @@ inline ScratchLayout make_layout(int max_m, int max_n, int team) {
   L.yJ = take(KM);
   L.pr = take(KM);
   L.part = take((size_t)team * PW);
+  L.pacc = take(3 * PACC_W);
   L.candw = take((size_t)team * KM);
   L.rotc = take(cap);
   L.rots = take(cap);
@@ -117,6 +118,7 @@ inline __host__ __device__ void bind_scratch(Inst& I, const ScratchLayout& L, do
   I.yJ = d + L.yJ;
   I.pr = d + L.pr;
   I.part = d + L.part;
+  I.pacc = reinterpret_cast<long long*>(d + L.pacc);
   I.candw = d + L.candw;
   I.rotc = d + L.rotc;
   I.rots = d + L.rots;

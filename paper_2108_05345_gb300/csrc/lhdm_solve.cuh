@@ -35,7 +35,6 @@ struct Engine {
   double wmax = 0.0, umax = 0.0, wz_any = -INFINITY, rsq = 0.0;
   double amax = 0.0, bsq = 0.0;
   int nonfinite = 0;
-  bool u_dirty = false;
   bool failed = false;
   bool vd_ok = false;  // the current panel's reflector digits are in Vd/Ver
   int kdm = 0, removed = 0, inner_step = 0;
@@ -159,6 +158,8 @@ struct Engine {
       I.order[p] = -1;
     }
     if (tm.rank == 0 && tid < 16) I.ctl[tid] = 0;
+    if (tm.rank == 0)
+      for (int e = tid; e < PACC_W; e += NT) I.pacc[e] = 0;  // the panel exchange's first sums
     if (tm.rank == 0 && tid == 0 && I.phase_ns) I.phase_ns[2 * NPHASE] = 0.0;  // MMA count
     clear_tri_flags();
     am = block_max(am, sh);
@@ -657,22 +658,28 @@ struct Engine {
   // Panel with the team's rows held in shared memory (at most PR_MAX rows
   // per CTA): the same Householder steps as panel(), one barrier per
   // reflector.  Each CTA keeps rows [q0, q1) of the kk selected columns and
-  // of Q^T b (column kk) for the whole panel; per reflector i it publishes
-  // its dots and, if it owns row i, the pivot row, and after the barrier
-  // every CTA reduces the team's dots itself (fixed order).  The scalars of
+  // of Q^T b (column kk) for the whole panel; per reflector i it adds its
+  // dots into the team's fixed-point sums at L2 and, if it owns row i,
+  // publishes the pivot row; after the barrier every CTA reads the sums
+  // (no CTA adds the team's partials itself: one FP64 add is 64 cycles of
+  // a sub-partition on this GPU, and every CTA would repeat them).  The scalars of
   // a reflector are formed once per CTA and shared; T is built by rank 0
   // after the last reflector from the saved products z_s = v_s^T v_i.
   // (FP64 issue is the scarce resource here: every warp instruction counts.)
   static constexpr int PR_MAX = 128;     // rows per CTA of the shared-memory panel
   static constexpr int PANEL_ROWS = 32;  // target rows per panel CTA
   static constexpr int PS = KM + 1;  // row stride of the staged panel
-  static constexpr int RED_U = 12;   // partial-sum loads in flight per thread
   __device__ bool panel_smem(const int* s_J, int P) {
     const int L = I.m - nP;
     if (kk > L) kk = L;
     if (tm.rank < P && !panel_rows(s_J, P, L)) return false;
     if (tm.rank == 0 && tid == 0) I.ctl[C_KK] = kk;
     if (!sync()) return false;
+    tm.sub_reset();
+    // every exchange sum is read: the next panel's first exchange adds into
+    // buffer 0 again
+    if (tm.rank == 0)
+      for (int e = tid; e < PACC_W; e += NT) I.pacc[e] = 0;
     kk = ldcg(I.ctl + C_KK);
     vd_ok = I.Vd != nullptr && kk > 4 && kk <= 32;
     return true;
@@ -698,6 +705,23 @@ struct Engine {
       sP[rr * PS + l] = (l < k0) ? ldcg(Wcol(s_J[l]) + nP + q0 + rr) : ldcg(I.bt + nP + q0 + rr);
     }
     if (tid < k0) s_an[tid] = ldcg(I.anorm + s_J[tid]);
+    // Exponent bounds of the panel columns' norms: u_j for a selected
+    // column (its trailing norm; the reflectors are orthogonal, so no part
+    // of the column below a pivot is longer) and ||b|| for Q^T b.  The dot
+    // of panel columns l and l' over any rows is below 2^(s_ex[l] + s_ex[l']),
+    // and half of that with the + 1 that the exchange adds.
+    __shared__ int s_ex[KM + 1];
+    if (tid < k0) s_ex[tid] = max(ebound(ldcg(I.u + s_J[tid])), -1000);
+    if (tid == k0) s_ex[tid] = max(ebound(sqrt(bsq)), -1000);
+    // The team's sums of an exchange are added up at L2 as fixed-point
+    // integers in units of 2^-55 of that bound (exact and order-free, so
+    // every run gives the same bits; the truncation of the P partials is
+    // below P 2^-53 u_l u_l', FP64's own bound for adding them), into
+    // buffer step mod 3, spread over PACC_COPIES copies to cut the
+    // contention on each word; rank 0 zeroes the buffer of the next
+    // exchange, whose previous readers all passed the barrier before this one.
+    const bool solo = P == 1;  // one CTA: its own sums are the team's
+    const int cp = (tm.rank % PACC_COPIES) * 2 * (KM + 1);
     __syncthreads();
     // owner of a panel row: the rank whose split range holds it
     auto owner = [&](int row) {
@@ -731,6 +755,8 @@ struct Engine {
     // rounding is of the order of the direct dots'.
     for (; i + 1 < k0; i += 2) {
       const int pb = (step & 1) * 4 * (KM + 1);
+      long long* acc = I.pacc + (step % 3) * PACC_W;
+      long long* acc_next = I.pacc + ((step + 1) % 3) * PACC_W;
       ++step;
       double* mypart = I.part + (size_t)tm.rank * PW;
       const int r0 = max(q0, i + 1) - q0, r1 = max(q0, i + 2) - q0;
@@ -753,10 +779,14 @@ struct Engine {
           }
           __syncthreads();
         }
-        if (tid <= k0) {
-          mypart[pb + tid] = sG[tid];
-          mypart[pb + (KM + 1) + tid] = sG[NT + tid];
+        if (!solo && tid <= k0) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(acc + cp + tid),
+                    (unsigned long long)fx_q(sG[tid], s_ex[i] + s_ex[tid] + 1));
+          atomicAdd(reinterpret_cast<unsigned long long*>(acc + cp + (KM + 1) + tid),
+                    (unsigned long long)fx_q(sG[NT + tid], s_ex[i + 1] + s_ex[tid] + 1));
         }
+        if (!solo && tm.rank == 0)
+          for (int e = tid; e < PACC_W; e += NT) acc_next[e] = 0;
       }
       if (i >= q0 && i < q1 && tid <= k0) mypart[pb + 2 * (KM + 1) + tid] = sP[(i - q0) * PS + tid];
       if (i + 1 >= q0 && i + 1 < q1 && tid <= k0) mypart[pb + 3 * (KM + 1) + tid] = sP[(i + 1 - q0) * PS + tid];
@@ -767,41 +797,17 @@ struct Engine {
           s_piv[tid] = ldcg(I.part + (size_t)own * PW + pb + 2 * (KM + 1) + tid);
           s_piv2[tid] = ldcg(I.part + (size_t)own2 * PW + pb + 3 * (KM + 1) + tid);
         }
-        if (actg) {
-          // ranks gg, gg + G, ...: every load of a round in flight at once
-          const int cnt = (P - gg + G - 1) / G;
-          double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
-          for (int j0 = 0; j0 < cnt; j0 += RED_U) {
-            double v[RED_U], w[RED_U];
+        if (!solo && tid <= k0) {
+          long long qg = 0, qk = 0;
 #pragma unroll
-            for (int k = 0; k < RED_U; ++k) {
-              const size_t o = (size_t)(gg + (j0 + k) * G) * PW + pb + gl;
-              v[k] = (j0 + k < cnt) ? ldcg(I.part + o) : 0.0;
-              w[k] = (j0 + k < cnt) ? ldcg(I.part + o + (KM + 1)) : 0.0;
-            }
-#pragma unroll
-            for (int k = 0; k < RED_U; k += 2) {
-              if (j0 + k < cnt) {
-                a0 += v[k];
-                c0 += w[k];
-              }
-              if (j0 + k + 1 < cnt) {
-                a1 += v[k + 1];
-                c1 += w[k + 1];
-              }
-            }
+          for (int c = 0; c < PACC_COPIES; ++c) {
+            qg += __ldcg(acc + c * 2 * (KM + 1) + tid);
+            qk += __ldcg(acc + c * 2 * (KM + 1) + (KM + 1) + tid);
           }
-          sG[gg * NL + gl] = a0 + a1;
-          sG[NT + gg * NL + gl] = c0 + c1;
+          sG[tid] = fx_x(qg, s_ex[i] + s_ex[tid] + 1);
+          sG[NT + tid] = fx_x(qk, s_ex[i + 1] + s_ex[tid] + 1);
         }
         __syncthreads();
-        for (int st = 1; st < G; st <<= 1) {
-          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) {
-            sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
-            sG[NT + gg * NL + gl] += sG[NT + (gg + st) * NL + gl];
-          }
-          __syncthreads();
-        }
       }
       // reflector i
       if (warp == 0 && lane == 0) {
@@ -923,6 +929,8 @@ struct Engine {
     }
     for (; i < k0 && !stopped; ++i) {
       const int pb = (step & 1) * 4 * (KM + 1);
+      long long* acc = I.pacc + (step % 3) * PACC_W;
+      long long* acc_next = I.pacc + ((step + 1) % 3) * PACC_W;
       ++step;
       double* mypart = I.part + (size_t)tm.rank * PW;
       // dots of column i with every column (and Q^T b) over own rows > i:
@@ -938,37 +946,25 @@ struct Engine {
           if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
           __syncthreads();
         }
-        if (tid <= k0) mypart[pb + tid] = sG[tid];
+        if (!solo && tid <= k0)
+          atomicAdd(reinterpret_cast<unsigned long long*>(acc + cp + tid),
+                    (unsigned long long)fx_q(sG[tid], s_ex[i] + s_ex[tid] + 1));
+        if (!solo && tm.rank == 0)
+          for (int e = tid; e < PACC_W; e += NT) acc_next[e] = 0;
       }
       if (i >= q0 && i < q1 && tid <= k0) mypart[2 * (KM + 1) + pb + tid] = sP[(i - q0) * PS + tid];
       if (!tm.sync_sub(P)) return false;
-      // every CTA reduces the team's dots: thread (gl, gg) adds ranks gg,
-      // gg + G, ... (loads first), then a pairwise tree over gg; the pivot
-      // row comes from its owner
+      // the team's dots from the fixed-point sums; the pivot row from its owner
       {
         const int own = s_own[i];
         if (tid <= k0) s_piv[tid] = ldcg(I.part + (size_t)own * PW + 2 * (KM + 1) + pb + tid);
-        if (actg) {
-          const int cnt = (P - gg + G - 1) / G;
-          double a0 = 0.0, a1 = 0.0;
-          for (int j0 = 0; j0 < cnt; j0 += RED_U) {
-            double v[RED_U];
+        if (!solo && tid <= k0) {
+          long long qg = 0;
 #pragma unroll
-            for (int k = 0; k < RED_U; ++k)
-              v[k] = (j0 + k < cnt) ? ldcg(I.part + (size_t)(gg + (j0 + k) * G) * PW + pb + gl) : 0.0;
-#pragma unroll
-            for (int k = 0; k < RED_U; k += 2) {
-              if (j0 + k < cnt) a0 += v[k];
-              if (j0 + k + 1 < cnt) a1 += v[k + 1];
-            }
-          }
-          sG[gg * NL + gl] = a0 + a1;
+          for (int c = 0; c < PACC_COPIES; ++c) qg += __ldcg(acc + c * 2 * (KM + 1) + tid);
+          sG[tid] = fx_x(qg, s_ex[i] + s_ex[tid] + 1);
         }
         __syncthreads();
-        for (int st = 1; st < G; st <<= 1) {
-          if (actg && (gg & (2 * st - 1)) == 0 && gg + st < G) sG[gg * NL + gl] += sG[(gg + st) * NL + gl];
-          __syncthreads();
-        }
       }
       // the reflector's scalars, once per CTA (warp 0), and f for every column
       if (warp == 0) {
@@ -2515,7 +2511,6 @@ struct Engine {
         const int q = ldcg(I.qlist + k);
         if (!delete_position(q)) return false;
       }
-      u_dirty = true;
       // re-solve: rhs = (Q^T b)[0:nP] was written by the owner of b
       phase(PH_ITRSV);
       if (!trsv(nP)) return false;
@@ -2540,6 +2535,8 @@ struct Engine {
       const int sq = ldcg(I.rslot + q);
       double* wc = Wcol(c);
       for (int i = tid; i < I.m; i += NT) wc[i] = (i <= q) ? ldcg(Rcol(sq) + i) : 0.0;
+      // its trailing norm is built up below like every Z column's
+      if (tid == 0) I.u[c] = 0.0;
       // shift positions q+1..np-1 down by one (read all, then write all)
       const int cnt = np - 1 - q;
       constexpr int PER = 8;  // positions per thread per sweep
@@ -2917,6 +2914,21 @@ struct Engine {
           }
           // an R column's last rotation zeroes the entry below its diagonal
           if (lane == 0) colp[q + rb + nsu] = rlast ? 0.0 : carry;
+          // row nP (the last carry) joins a Z column's trailing part: its
+          // norm grows by that entry (an update, free of cancellation)
+          if (lane == 0 && k < s_nz && rb + ns == nrot) {
+            const int c = s_zl[k];
+            const double uo = ldcg(I.u + c);
+            I.u[c] = sqrt(fma(carry, carry, uo * uo));
+          }
+        }
+      }
+      if (nrot == 0) {
+        // the last position went: row nP joins the trailing part unrotated
+        for (int k = tid; k < s_nz; k += NT) {
+          const int c = s_zl[k];
+          const double v = ldcg(Wcol(c) + nP), uo = ldcg(I.u + c);
+          I.u[c] = sqrt(fma(v, v, uo * uo));
         }
       }
       // the triangular solve that follows reads rhs = (Q^T b)[0:nP]
@@ -2955,9 +2967,16 @@ struct Engine {
       if (row < I.m) {
         int p = warp;
         if (staged) {
-          for (; p + NW < nP; p += 2 * NW) {
-            acc = fma(__ldg(I.A + (size_t)s_ov[p] * I.lda + row), s_yv[p], acc);
-            acc2 = fma(__ldg(I.A + (size_t)s_ov[p + NW] * I.lda + row), s_yv[p + NW], acc2);
+          // eight columns' loads in flight per lane
+          for (; p + 7 * NW < nP; p += 8 * NW) {
+            double av[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) av[j] = __ldg(I.A + (size_t)s_ov[p + j * NW] * I.lda + row);
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+              acc = fma(av[j], s_yv[p + j * NW], acc);
+              acc2 = fma(av[j + 1], s_yv[p + (j + 1) * NW], acc2);
+            }
           }
           for (; p < nP; p += NW) acc = fma(__ldg(I.A + (size_t)s_ov[p] * I.lda + row), s_yv[p], acc);
         } else {
@@ -2991,11 +3010,15 @@ struct Engine {
     if (tid == 0) I.part[(size_t)tm.rank * PW + P_RS] = rs;
   }
 
-  // w = A^T r on Z (w_P = 0), u refreshed after removals, O1 partial.  The
-  // Z columns are split evenly over the team (z_share) and r is staged in
-  // shared memory; in batches of up to 32 columns, warps take (column,
-  // quarter of the rows) units round-robin and each column's four quarters
-  // are added in a fixed order.
+  // w = A^T r on Z (w_P = 0) and the O1 partial.  The Z columns are split
+  // evenly over the team (z_share) and r is staged in shared memory; the
+  // CTA's nl x m elements, in column order, are split evenly over its warps
+  // (one FP64 instruction per warp is 64 cycles on this GPU whatever the
+  // active lanes, so equal shares keep every sub-partition's FP64 pipe busy
+  // to the end).  A column inside one warp's share is summed by that warp; a
+  // column cut by share boundaries gets its partial sums added in warp
+  // order.  The trailing norms u need no pass here: the downdate updates
+  // them as it moves a row into the trailing part.
   static constexpr int DUAL_RMAX = 16384;  // rows of r held in shared memory
   __device__ void dual() {
     {
@@ -3010,30 +3033,22 @@ struct Engine {
     double* s_r = dyn;                                    // m doubles
     int* s_zl = reinterpret_cast<int*>(dyn + (r_in_smem ? m : 0));
     unsigned* scr = reinterpret_cast<unsigned*>(s_zl + CAND_LOCAL_MAX + 2);
-    __shared__ double s_pw[32 * 4], s_pu[32 * 4];
-    __shared__ int s_c[32];
+    __shared__ double s_pp[NW][2];  // partial sums of a warp's first and last column
     const int nl = z_share(s_zl, scr, nullptr, 0, false);
     if (r_in_smem)
       for (int i = tid; i < m; i += NT) s_r[i] = ldcg(I.r + i);
+    __syncthreads();
     const double* rv = r_in_smem ? s_r : I.r;
-    const int L = m - nP;
-    for (int base = 0; base < nl; base += 32) {
-      const int nb = min(32, nl - base);
-      __syncthreads();
-      if (tid < nb) s_c[tid] = s_zl[base + tid];
-      __syncthreads();
-      const int nunit = (u_dirty ? 8 : 4) * nb;
-      for (int un = warp; un < nunit; un += NW) {
-        const bool is_u = un >= 4 * nb;
-        const int k = (is_u ? un - 4 * nb : un) >> 2, qq = un & 3;
-        const int c = s_c[k];
-        double sa[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) sa[j] = 0.0;
-        if (!is_u) {
-          const double* a = I.A + (size_t)c * I.lda;
-          int i0, i1;
-          split(m, 4, qq, i0, i1);
+    const long long E = (long long)nl * m;
+    {
+      const long long e0 = E * warp / NW, e1 = E * (warp + 1) / NW;
+      if (e0 < e1) {
+        const int kf = (int)(e0 / m), kl = (int)((e1 - 1) / m);
+        for (int k = kf; k <= kl; ++k) {
+          const int i0 = (k == kf) ? (int)(e0 - (long long)k * m) : 0;
+          const int i1 = (k == kl) ? (int)(e1 - (long long)k * m) : m;
+          const double* a = I.A + (size_t)s_zl[k] * I.lda;
+          double s0 = 0.0, s1 = 0.0;
           int i = i0 + lane;
           for (; i + 224 < i1; i += 256) {
             double av[8], rr[8];
@@ -3043,38 +3058,37 @@ struct Engine {
               rr[j] = r_in_smem ? rv[i + 32 * j] : ldcg(rv + i + 32 * j);
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) sa[j] = fma(av[j], rr[j], sa[j]);
+            for (int j = 0; j < 8; j += 2) {
+              s0 = fma(av[j], rr[j], s0);
+              s1 = fma(av[j + 1], rr[j + 1], s1);
+            }
           }
-          for (; i < i1; i += 32) sa[0] = fma(__ldg(a + i), r_in_smem ? rv[i] : ldcg(rv + i), sa[0]);
-        } else {
-          const double* wc = Wcol(c) + nP;
-          int i0, i1;
-          split(L, 4, qq, i0, i1);
-          int i = i0 + lane;
-          for (; i + 224 < i1; i += 256) {
-            double v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = ldcg(wc + i + 32 * j);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) sa[j] = fma(v[j], v[j], sa[j]);
-          }
-          for (; i < i1; i += 32) {
-            const double v0 = ldcg(wc + i);
-            sa[0] = fma(v0, v0, sa[0]);
+          for (; i < i1; i += 32) s0 = fma(__ldg(a + i), r_in_smem ? rv[i] : ldcg(rv + i), s0);
+          const double tot = warp_sum(s0 + s1);
+          if (lane == 0) {
+            if (k == kf) s_pp[warp][0] = tot;
+            else if (k == kl) s_pp[warp][1] = tot;
+            else I.w[s_zl[k]] = tot;
           }
         }
-        const double tot = warp_sum(((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7])));
-        if (lane == 0) (is_u ? s_pu : s_pw)[k * 4 + qq] = tot;
       }
-      __syncthreads();
-      if (tid < nb) {
-        const double* pw = s_pw + tid * 4;
-        I.w[s_c[tid]] = (pw[0] + pw[1]) + (pw[2] + pw[3]);
-        if (u_dirty) {
-          const double* pu = s_pu + tid * 4;
-          I.u[s_c[tid]] = sqrt((pu[0] + pu[1]) + (pu[2] + pu[3]));
+    }
+    __syncthreads();
+    for (int k = tid; k < nl; k += NT) {
+      const long long cs = (long long)k * m, ce = cs + m;
+      double sum = 0.0;
+      bool direct = false;
+      for (int w = 0; w < NW; ++w) {
+        const long long a0 = E * w / NW, a1 = E * (w + 1) / NW;
+        if (a0 >= a1 || a1 <= cs || a0 >= ce) continue;
+        const int kf = (int)(a0 / m), kl = (int)((a1 - 1) / m);
+        if (k != kf && k != kl) {
+          direct = true;  // written by warp w
+          break;
         }
+        sum += (k == kf) ? s_pp[w][0] : s_pp[w][1];
       }
+      if (!direct) I.w[s_zl[k]] = sum;
     }
     // resid sum of squares of this CTA is in part[PW-1]; fold it into slot 6
     const double rs = ldcg(I.part + (size_t)tm.rank * PW + P_RS);
@@ -3228,7 +3242,6 @@ struct Engine {
       phase(PH_COMMIT);
       if (!commit(s_J)) return fail_out();
       phase(PH_INNER);
-      u_dirty = false;
       removed = 0;
       inner_step = 0;
       if (!inner_loop()) return fail_out();
@@ -3238,7 +3251,7 @@ struct Engine {
       residual();
       if (!sync()) return fail_out();
       phase(PH_DUAL);
-      flops(PH_DUAL, (u_dirty ? 4.0 : 2.0) * (double)I.m * (double)(I.n - nP));
+      flops(PH_DUAL, 2.0 * (double)I.m * (double)(I.n - nP));
       dual();
       if (!sync()) return fail_out();
       if (I.trace && tm.rank == 0 && tid == 0 && n_outer < I.trace_cap) {
