@@ -322,6 +322,18 @@ int lhdm_debug_commit_guard(lhdm_ctx* ctx, int32_t mode);
  */
 int lhdm_debug_stall_next_solve(lhdm_ctx* ctx);
 
+/*
+ * Verification aid for the reciprocal and square root the panel's scalar
+ * chains use in place of the compiler's correctly rounded ones (Newton-
+ * Raphson from a single-precision seed; Goldschmidt with a Newton
+ * correction).  For each of the n device doubles x[i], out (device, 4 n
+ * doubles) receives out[4i] = the panel's 1/x, out[4i+1] = 1.0/x,
+ * out[4i+2] = the panel's sqrt(|x|), out[4i+3] = sqrt(|x|), computed on the
+ * device on `stream`; the call does not synchronise.
+ * Errors: INVALID_ARG (n < 0, or a null pointer with n > 0), CUDA.
+ */
+int lhdm_debug_fast_math(const double* x, double* out, int32_t n, void* stream);
+
 /* Decision trace of the last solve (verification aid): up to max_rows rows
  * of 6 int32 per outer step, host buffer out[6 * max_rows]:
  *   |J| from Algorithm 2, |J| kept after the feasibility loop, inner-loop

@@ -503,6 +503,23 @@ int lhdm_debug_stall_next_solve(lhdm_ctx* c) {
   return LHDM_OK;
 }
 
+__global__ void lhdm_fast_math_kernel(const double* __restrict__ x, double* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i], a = fabs(v);
+  out[4 * i] = rcp_nr(v);
+  out[4 * i + 1] = 1.0 / v;
+  out[4 * i + 2] = sqrt_gm(a);
+  out[4 * i + 3] = sqrt(a);
+}
+
+int lhdm_debug_fast_math(const double* x, double* out, int32_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return LHDM_ERR_INVALID_ARG;
+  if (n == 0) return LHDM_OK;
+  lhdm_fast_math_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? LHDM_OK : LHDM_ERR_CUDA;
+}
+
 // ----------------------------------------------------------------------- allocation-free solve
 // Callers that cannot allocate device memory (see lhdm_solve_noalloc) use one
 // workspace that lives in a file-scope device array for the life of the

@@ -369,6 +369,79 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (x * pow2n(e1)) * pow2n(e - e1);
 }
 
+// u 2^es, rounded once to nearest (ties to even) like scale2((double)u, es),
+// built with integer instructions: on this GPU a conversion to FP64 costs
+// one instruction of the FP64 pipe, which the integer pipe does not share.
+// Results outside the normal range take the FP64 route.
+__device__ __forceinline__ double ll_scaled(long long u, int es) {
+  if (u == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)u & 0x8000000000000000ull;
+  unsigned long long a = (u < 0) ? 0ull - (unsigned long long)u : (unsigned long long)u;
+  const int lz = __clzll(a);
+  int e = 63 - lz + es + 1023;  // biased exponent of the leading bit
+  if (e < 1 || e > 2045) return scale2((double)u, es);
+  a <<= lz;
+  unsigned long long m = a >> 11;  // 53 bits, leading bit set
+  const unsigned rem = (unsigned)(a & 0x7FFull);
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  if (m >> 53) {  // rounded up to the next power of two
+    m >>= 1;
+    ++e;
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// Reciprocal and square root for the scalar chains of the panel.  On this
+// GPU one FP64 instruction is 64 cycles of a sub-partition, and the
+// correctly rounded division and square root of the compiler take about ten
+// each; these take four and five on the dependent path.  The seed is the
+// single-precision hardware approximation (rcp.approx / rsqrt.approx, about
+// 2^-22) of the mantissa, rebuilt as a double with integer instructions;
+// then, for 1/d, two Newton-Raphson steps y += y (1 - d y) (each squares
+// the relative error), and for sqrt(s) one Goldschmidt step on (g, h) =
+// (s y, y / 2) followed by a Newton correction with the exact remainder
+// s - g^2 (Markstein's scheme).  Both end within about one ulp of the
+// correctly rounded result (lhdm_debug_fast_math checks this against the
+// library's).  Arguments outside the normal range, zero and non-finite ones
+// take the library's routines.
+__device__ __forceinline__ double rcp_nr(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)((b >> 52) & 0x7FFu) - 1023;
+  if (E < -1000 || E > 1000) return 1.0 / d;  // also zero, subnormal, inf, nan
+  float r;
+  const float mf = __uint_as_float(0x3F800000u | (unsigned)((b >> 29) & 0x7FFFFFull));  // |mantissa| in [1, 2)
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mf));
+  const unsigned rb = __float_as_uint(r);
+  const long long ye = (long long)(((rb >> 23) & 0xFFu) - 127 - E + 1023);
+  double y = __longlong_as_double((long long)(b & 0x8000000000000000ull) | (ye << 52) |
+                                  ((long long)(rb & 0x7FFFFFu) << 29));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double sqrt_gm(double s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int E = (int)((b >> 52) & 0x7FFu) - 1023;
+  if (!(s > 0.0) || E < -1000 || E > 1000) return sqrt(s);
+  // s = f 2^(2k), f in [1, 4): the seed is rsqrt(f) 2^-k
+  const int k = E >> 1;  // floor(E / 2)
+  const unsigned fe = (unsigned)(E - 2 * k);  // 0 or 1
+  const float mf = __uint_as_float(((127u + fe) << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mf));
+  const unsigned rb = __float_as_uint(r);
+  const long long ye = (long long)((rb >> 23) & 0xFFu) - 127 - k + 1023;
+  const double y = __longlong_as_double((ye << 52) | ((long long)(rb & 0x7FFFFFu) << 29));
+  const double hy = __longlong_as_double(((ye - 1) << 52) | ((long long)(rb & 0x7FFFFFu) << 29));  // y / 2
+  double g = s * y;
+  const double r1 = fma(-g, hy, 0.5);
+  g = fma(g, r1, g);
+  const double h = fma(hy, r1, hy);
+  const double dr = fma(-g, g, s);
+  return fma(dr, h, g);
+}
+
 // x with |x| <= 2^(E-1) as a fixed-point integer in units of 2^(E-56)
 // (truncated; |q| <= 2^55).  Such integers add exactly and in any order to
 // the same sum, and up to 256 of them fit in 64 bits.
@@ -451,12 +524,25 @@ struct CtaTeam {
   __device__ __forceinline__ void sub_reset() {}
 };
 
+// Flags between CTAs.  A CTA publishes with one thread after a CTA barrier
+// (the release covers what every thread wrote before that barrier); a
+// waiting thread acquires, and a CTA barrier after the wait passes the
+// values on to the other threads.
+__device__ __forceinline__ void flag_release(int* flag, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flag), "r"(v) : "memory");
+}
+__device__ __forceinline__ int flag_acquire(const int* flag) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+  return v;
+}
+
 // Bounded wait until *flag >= target (one thread); false on timeout.
 __device__ __forceinline__ bool wait_ge(const int* flag, int target, int* err, long long wait_ns) {
-  if (*(volatile const int*)flag >= target) return true;
+  if (flag_acquire(flag) >= target) return true;
   const long long t0 = gtimer();
   unsigned int spins = 0;
-  while (*(volatile const int*)flag < target) {
+  while (flag_acquire(flag) < target) {
     if ((++spins & 63u) == 0u) {
       if (err && *(volatile int*)err) return false;
       if (gtimer() - t0 > wait_ns) {
@@ -465,7 +551,6 @@ __device__ __forceinline__ bool wait_ge(const int* flag, int target, int* err, l
       }
     }
   }
-  __threadfence();
   return true;
 }
 

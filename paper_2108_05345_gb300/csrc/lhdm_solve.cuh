@@ -558,12 +558,12 @@ struct Engine {
         __syncthreads();
       }
       const double xii = ldcg(V + (size_t)i * KM + i);
-      const double alpha = sqrt(xii * xii + s_sum[i]);
+      const double alpha = sqrt_gm(xii * xii + s_sum[i]);
       const double an = ldcg(I.anorm + s_J[i]);
       if (i >= L || !(alpha > (100.0 * EPS) * an)) break;
       const double sg = (xii >= 0.0) ? 1.0 : -1.0;
       const double v0 = xii + sg * alpha;
-      const double beta = 2.0 / (v0 * v0 + s_sum[i]);
+      const double beta = 2.0 * rcp_nr(v0 * v0 + s_sum[i]);
       if (tid <= k0) {
         double f = 0.0;
         if (tid > i && tid < k0) f = beta * (v0 * ldcg(V + (size_t)i * KM + tid) + s_sum[tid]);
@@ -812,14 +812,14 @@ struct Engine {
       // reflector i
       if (warp == 0 && lane == 0) {
         const double xii = s_piv[i], ssum_i = sG[i];
-        const double alpha = sqrt(fma(xii, xii, ssum_i));
+        const double alpha = sqrt_gm(fma(xii, xii, ssum_i));
         const int stop = (i >= L || !(alpha > (100.0 * EPS) * s_an[i])) ? 1 : 0;
         const double sg = (xii >= 0.0) ? 1.0 : -1.0;
         const double v0 = xii + sg * alpha;
         s_stop = stop;
         s_sc[0] = alpha;
         s_sc[1] = v0;
-        s_sc[2] = stop ? 0.0 : 2.0 / fma(v0, v0, ssum_i);
+        s_sc[2] = stop ? 0.0 : 2.0 * rcp_nr(fma(v0, v0, ssum_i));
         s_sc[3] = sg;
       }
       __syncthreads();
@@ -853,14 +853,14 @@ struct Engine {
       // reflector i+1 on the columns after reflector i
       if (warp == 0 && lane == 0) {
         const double xii = s_xp[i + 1], ssum_i = s_H[i + 1];
-        const double alpha = sqrt(fma(xii, xii, ssum_i));
+        const double alpha = sqrt_gm(fma(xii, xii, ssum_i));
         const int stop = (i + 1 >= L || !(alpha > (100.0 * EPS) * s_an[i + 1])) ? 1 : 0;
         const double sg = (xii >= 0.0) ? 1.0 : -1.0;
         const double v0b = xii + sg * alpha;
         s_stop2 = stop;
         s_sc[4] = alpha;
         s_sc[5] = v0b;
-        s_sc[6] = stop ? 0.0 : 2.0 / fma(v0b, v0b, ssum_i);
+        s_sc[6] = stop ? 0.0 : 2.0 * rcp_nr(fma(v0b, v0b, ssum_i));
         s_sc[7] = sg;
       }
       __syncthreads();
@@ -971,14 +971,14 @@ struct Engine {
         const double ssum_i = sG[i];
         if (lane == 0) {
           const double xii = s_piv[i];
-          const double alpha = sqrt(fma(xii, xii, ssum_i));
+          const double alpha = sqrt_gm(fma(xii, xii, ssum_i));
           const int stop = (i >= L || !(alpha > (100.0 * EPS) * s_an[i])) ? 1 : 0;
           const double sg = (xii >= 0.0) ? 1.0 : -1.0;
           const double v0 = xii + sg * alpha;
           s_stop = stop;
           s_sc[0] = alpha;
           s_sc[1] = v0;
-          s_sc[2] = stop ? 0.0 : 2.0 / fma(v0, v0, ssum_i);
+          s_sc[2] = stop ? 0.0 : 2.0 * rcp_nr(fma(v0, v0, ssum_i));
           s_sc[3] = sg;
         }
       }
@@ -1385,12 +1385,9 @@ struct Engine {
           ycur[row] = (s01 + s23) + (s45 + s67);
         }
       }
-      if (g == 0 && row < nbk) {
-        I.yP[b0 + row] = ycur[row];
-        __threadfence();
-      }
+      if (g == 0 && row < nbk) I.yP[b0 + row] = ycur[row];
       __syncthreads();
-      if (tid == 0) atomicExch(yfl + bi, ep);
+      if (tid == 0) flag_release(yfl + bi, ep);
     }
     return true;
   }
@@ -1431,13 +1428,10 @@ struct Engine {
       __syncthreads();
       if (warp < SLAB) {
         const double t = warp_sum(s_red[lane * SLAB + warp]);
-        if (lane == 0) {
-          I.accb[r0 + warp] = t;
-          __threadfence();
-        }
+        if (lane == 0) I.accb[r0 + warp] = t;
       }
       __syncthreads();
-      if (tid == 0) atomicExch(sfl + s, ep);
+      if (tid == 0) flag_release(sfl + s, ep);
     }
     return true;
   }
@@ -1498,10 +1492,9 @@ struct Engine {
         double* out = I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB;
         out[lane] = (lane <= j) ? a0 : 0.0;
         out[lane + 32] = (lane + 32 <= j) ? a1 : 0.0;
-        __threadfence();
       }
       __syncthreads();
-      if (tid == 0) atomicExch(ifl + bi * PARTS + part, ep);
+      if (tid == 0) flag_release(ifl + bi * PARTS + part, ep);
     }
   }
 
@@ -2174,7 +2167,7 @@ struct Engine {
             u += (long long)(__float2int_rn(a2[7][j]) >> 6);
             u += (long long)(__float2int_rn(a2[8][j]) >> 13);
             const int es = max(-2044, ((j < 2) ? er0 : er1) + s_Ee[c] - 57);
-            const double x = xv[j] - scale2((double)u, es);
+            const double x = xv[j] - ll_scaled(u, es);
             p[row] = x;
             if (row >= kp) {
               if (j & 1) nrm1 = fma(x, x, nrm1);

@@ -77,6 +77,7 @@ def lib():
         L.lhdm_solve_l1.argtypes = [V, i32, i32, d, i32, d, C.c_double, P, d, d, I, V]
         L.lhdm_debug_stall_next_solve.argtypes = [V]
         L.lhdm_debug_commit_guard.argtypes = [V, i32]
+        L.lhdm_debug_fast_math.argtypes = [V, V, i32, V]
         L.lhdm_phase_times.argtypes = [V, C.POINTER(C.c_double), i32, V]
         L.lhdm_trace.argtypes = [V, C.POINTER(C.c_int32), i32, V]
         L.lhdm_debug_state.argtypes = [V, C.c_char_p, C.c_void_p, C.c_int64, V]
@@ -165,6 +166,17 @@ def solve_noalloc(A, b, params=None, x=None, passive=None, info=None, stream=Non
                                   x.data_ptr() if n else None, passive.data_ptr() if n else None,
                                   info.data_ptr(), _stream(stream))
     return rc, x, passive, info
+
+
+def fast_math(x, stream=None):
+    """lhdm_debug_fast_math on a CUDA float64 tensor x: an (n, 4) tensor of
+    (panel 1/x, 1.0/x, panel sqrt|x|, sqrt|x|)."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty((x.numel(), 4), dtype=torch.float64, device=x.device)
+    _check(lib().lhdm_debug_fast_math(x.data_ptr(), out.data_ptr(), x.numel(), _stream(stream)),
+           "lhdm_debug_fast_math")
+    return out
 
 
 def info_from_device(buf):

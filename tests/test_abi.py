@@ -49,6 +49,8 @@ def test_host_only_validation(lib):
     assert L.lhdm_backward_batched(None, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_set_wait_limit(None, 5) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_debug_commit_guard(None, 1) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_debug_fast_math(None, None, 3, None) == lhdm.LHDM_ERR_INVALID_ARG
+    assert L.lhdm_debug_fast_math(None, None, -1, None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_solve_l1(None, 1, 1, None, 1, None, 1.0, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_solve(None, 1, 1, None, 1, None, None, None, None, None, None) == lhdm.LHDM_ERR_INVALID_ARG
     assert L.lhdm_destroy(None) == lhdm.LHDM_ERR_INVALID_ARG
