@@ -1260,47 +1260,73 @@ struct Engine {
   __device__ __forceinline__ int* sflags() const { return I.tflag + (I.cap + TB - 1) / TB; }
   __device__ __forceinline__ int* iflags() const { return I.tflag + (1 + TB / SLAB) * ((I.cap + TB - 1) / TB); }
 
-  // Rank 0: the chain over the blocks (see trsv_pipelined).
+  // Rank 0: the chain over the blocks (see trsv_pipelined).  What a block
+  // reads without waiting for y - its slots, the tile R(b, b+1), the
+  // inverse columns cached by earlier solves and rhs - is copied to shared
+  // memory (cp.async) while the block before it in the chain (b + 1)
+  // finishes, so that a block waits only for the slab sums.
   __device__ bool tri_chain(int np, int nb, int ep) {
     double* sD = dyn;                       // TB x (TB+1) stale diagonal columns
     double* sP = dyn + TB * (TB + 1);       // 8 x TB partial sums
+    double* sRT = sP + 8 * TB;              // TB x TB: R(b, b+1), column j at j TB
+    double* sDI = sRT + TB * TB;            // TB x TB: the cached inverse columns
+    __shared__ double s_rh[TB];
     __shared__ double s_a[TB];
     __shared__ double s_y[2][TB];
     __shared__ double s_rinv[TB];
-    __shared__ int s_bslot[TB], s_cslot[TB];
+    __shared__ int s_slot[2][TB];           // slots of block bi in s_slot[bi & 1]
     const int row = tid & (TB - 1), g = tid >> 6;  // 8 groups of 8 columns
     int* yfl = yflags();
     const int* sfl = sflags();
     const int* ifl = iflags();
+    int pslot = 0;
+    auto valid_cols = [&](int b0, int nbk) { return min(max(inv_valid - b0, 0), nbk); };
+    // block bi's loads that wait for nothing (its columns' slots are those
+    // of block bi + 1, already in s_slot)
+    auto prefetch = [&](int bi) {
+      const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
+      const int nc = (bi + 1 < nb) ? min(np, b0 + 2 * TB) - (b0 + TB) : 0;
+      const int v = valid_cols(b0, nbk);
+      const int* cs = s_slot[(bi + 1) & 1];
+      pslot = (tid < nbk) ? ldcg(I.rslot + b0 + tid) : 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = g * 8 + q;
+        const bool okr = row < nbk && j < nc, okd = row <= j && j < v;
+        cp8(sRT + j * TB + row, okr ? Rcol(cs[j]) + b0 + row : I.rhs, okr);
+        cp8(sDI + j * TB + row, okd ? I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB + row : I.rhs, okd);
+      }
+      if (g == 0) cp8(s_rh + row, row < nbk ? I.rhs + b0 + row : I.rhs, row < nbk);
+      cp_commit();
+    };
+    prefetch(nb - 1);
     for (int bi = nb - 1; bi >= 0; --bi) {
       const int b0 = bi * TB, nbk = min(np, b0 + TB) - b0;
-      const int c0 = b0 + TB, nc = (bi + 1 < nb) ? min(np, c0 + TB) - c0 : 0;
-      int v = min(max(inv_valid - b0, 0), nbk);  // columns with a valid inverse
+      const int nc = (bi + 1 < nb) ? min(np, b0 + 2 * TB) - (b0 + TB) : 0;
+      int v = valid_cols(b0, nbk);  // columns with a valid inverse
       double* ycur = s_y[bi & 1];
       const double* ynext = s_y[(bi + 1) & 1];
-      if (tid < nbk) s_bslot[tid] = ldcg(I.rslot + b0 + tid);
-      if (tid >= TB && tid - TB < nc) s_cslot[tid - TB] = ldcg(I.rslot + c0 + tid - TB);
+      int* s_bslot = s_slot[bi & 1];
+      if (tid < nbk) s_bslot[tid] = pslot;
+      cp_wait_all();  // this thread's copies of the block's operands
       if (bi < nb - 1 && v < nbk) {
         // the stale columns of this block are being inverted by the last
-        // ranks in this call: wait for them instead of substituting
+        // ranks in this call: wait for them instead of substituting, then
+        // read the whole block's inverse
         int okw = 1;
         if (tid < INV_PARTS) okw = wait_ge(ifl + bi * INV_PARTS + tid, ep, tm_err(), I.wait_ns) ? 1 : 0;
         if (!__syncthreads_and(okw)) return false;
         v = nbk;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = g * 8 + q;
+          sDI[j * TB + row] = (row <= j) ? ldcg(I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB + row) : 0.0;
+        }
       } else {
         __syncthreads();
       }
-      // loads that do not wait for y: tile R(b, b+1), inverse columns, rhs,
-      // stale columns of the diagonal block
-      double rt[8], di[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = g * 8 + q;
-        rt[q] = (row < nbk && j < nc) ? ldcg(Rcol(s_cslot[j]) + b0 + row) : 0.0;
-        di[q] = (row <= j && j < v) ? ldcg(I.Dinv + (size_t)bi * TB * TB + (size_t)j * TB + row) : 0.0;
-      }
-      const double rh = (g == 0 && row < nbk) ? ldcg(I.rhs + b0 + row) : 0.0;
       if (v < nbk) {
+        // stale columns of the diagonal block
         const int ns = (nbk - v) * TB;  // <= TB * TB = 8 per thread
         double sv[TB * TB / NT];
 #pragma unroll
@@ -1322,8 +1348,8 @@ struct Engine {
         double p0 = 0.0, p1 = 0.0;
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
-          p0 = fma(rt[q], ynext[g * 8 + q], p0);
-          p1 = fma(rt[q + 1], ynext[g * 8 + q + 1], p1);
+          p0 = fma(sRT[(g * 8 + q) * TB + row], ynext[g * 8 + q], p0);
+          p1 = fma(sRT[(g * 8 + q + 1) * TB + row], ynext[g * 8 + q + 1], p1);
         }
         sP[g * TB + row] = p0 + p1;
       }
@@ -1336,7 +1362,7 @@ struct Engine {
       }
       if (!__syncthreads_and(okw)) return false;
       if (g == 0 && row < nbk) {
-        double a = rh - acc;
+        double a = s_rh[row] - acc;
         if (nc > 0) {
           const double s01 = sP[row] + sP[TB + row], s23 = sP[2 * TB + row] + sP[3 * TB + row];
           const double s45 = sP[4 * TB + row] + sP[5 * TB + row], s67 = sP[6 * TB + row] + sP[7 * TB + row];
@@ -1373,8 +1399,8 @@ struct Engine {
 #pragma unroll
           for (int q = 0; q < 8; q += 2) {
             const int j = g * 8 + q;
-            if (j < v) p0 = fma(di[q], s_a[j], p0);
-            if (j + 1 < v) p1 = fma(di[q + 1], s_a[j + 1], p1);
+            if (j < v) p0 = fma(sDI[j * TB + row], s_a[j], p0);
+            if (j + 1 < v) p1 = fma(sDI[(j + 1) * TB + row], s_a[j + 1], p1);
           }
         }
         sP[g * TB + row] = p0 + p1;
@@ -1386,6 +1412,8 @@ struct Engine {
         }
       }
       if (g == 0 && row < nbk) I.yP[b0 + row] = ycur[row];
+      // the next block's loads go out before this block is published
+      if (bi > 0) prefetch(bi - 1);
       __syncthreads();
       if (tid == 0) flag_release(yfl + bi, ep);
     }
