@@ -696,7 +696,7 @@ struct Engine {
     double* sG = sZ + KM * KM;          // reduction scratch (2 NT doubles)
     double* sT = sG + 2 * NT;           // KM x KM, rank 0: T
     __shared__ double s_sum[KM + 1], s_f[KM + 1], s_piv[KM + 1], s_an[KM], s_bt[KM];
-    __shared__ double s_k[KM + 1], s_piv2[KM + 1], s_xp[KM + 1], s_A[KM + 1], s_H[KM + 1], s_f2[KM + 1];
+    __shared__ double s_k[KM + 1], s_piv2[KM + 1], s_xp[KM + 1], s_A[KM + 1], s_H[KM + 1], s_f2[KM + 1], s_g[KM + 1];
     __shared__ double s_sc[8];          // alpha, v0, beta, sign; the same for the second reflector
     __shared__ double s_v0[KM];         // v0 of every reflector (every CTA)
     __shared__ int s_stop, s_stop2;
@@ -869,6 +869,7 @@ struct Engine {
       if (tid == 0 && two) s_v0[i + 1] = v0b;
       if (tid <= k0) {
         s_f2[tid] = (two && tid > i + 1) ? beta2 * fma(v0b, s_xp[tid], s_H[tid]) : 0.0;
+        s_g[tid] = fma(-s_f2[tid], s_f[i + 1], s_f[tid]);
         if (tm.rank == 0 && tid < i) sZ[tid + i * KM] = fma(s_piv[tid], v0, s_sum[tid]);  // z_s = v_s^T v_i
         if (tm.rank == 0 && two && tid <= i) {
           // z_s = v_s^T v_{i+1}: v_s[i+1] v0' + x_s^T x'_{i+1} over rows > i+1
@@ -901,18 +902,21 @@ struct Engine {
       flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i) + 1) * (double)(L - i));
       if (two) flops(PH_PANEL, 2.0 * (double)(2 * (k0 - i - 1) + 1) * (double)(L - i - 1));
       // own rows: reflector i on rows > i (columns > i), then reflector i+1
-      // on rows > i+1 (columns > i+1); the row's column i+1 after reflector
-      // i is recomputed per element
-      // (columns i+2 .. first, reading column i+1 before it is updated)
+      // on rows > i+1 (columns > i+1), both in two FMAs per element from
+      // the row's columns i and i+1 before either reflector (columns i+2 ..
+      // first, reading column i+1 before it is updated)
       {
         const int nl = k0 - i - 1;
         for (int e = tid; e < (nr - r0) * nl; e += NT) {
           const int rr = r0 + e / nl, l = i + 2 + (e - (e / nl) * nl);
           const double xi = sP[rr * PS + i];
-          double x = fma(-s_f[l], xi, sP[rr * PS + l]);
+          double x;
           if (two && rr >= r1) {
-            const double xi1 = fma(-s_f[i + 1], xi, sP[rr * PS + i + 1]);
-            x = fma(-s_f2[l], xi1, x);
+            // x - f_l x_i - f2_l (x_{i+1} - f_{i+1} x_i), with g_l = f_l - f2_l f_{i+1}
+            x = fma(-s_g[l], xi, sP[rr * PS + l]);
+            x = fma(-s_f2[l], sP[rr * PS + i + 1], x);
+          } else {
+            x = fma(-s_f[l], xi, sP[rr * PS + l]);
           }
           sP[rr * PS + l] = x;
         }
@@ -2873,6 +2877,10 @@ struct Engine {
     {
       double* s_c = dyn;
       double* s_s = dyn + ROT_STAGE;
+      // the scan's multiplicative parts, the same for every column: per
+      // 32-rotation chunk, lane t's running product of -sin before each of
+      // the five levels (rows 0-4) and after the last (row 5)
+      double* s_am = dyn + 2 * ROT_STAGE;  // 6 x ROT_STAGE
       int c0, c1;
       split(I.n, tm.size, tm.rank, c0, c1);
       const bool do_b = (tm.rank == tm.size - 1);
@@ -2893,6 +2901,18 @@ struct Engine {
         for (int e = tid; e < ns; e += NT) {
           s_c[e] = ldcg(I.rotc + rb + e);
           s_s[e] = ldcg(I.rots + rb + e);
+        }
+        __syncthreads();
+        for (int t0 = warp * 32; t0 < ns; t0 += NW * 32) {
+          const int cnt = min(32, ns - t0);
+          double Am = (lane < cnt) ? -s_s[t0 + lane] : 1.0;
+#pragma unroll
+          for (int lv = 0; lv < 5; ++lv) {
+            s_am[lv * ROT_STAGE + t0 + lane] = Am;
+            const double Ap = __shfl_up_sync(0xffffffffu, Am, 1 << lv);
+            if (lane >= (1 << lv)) Am *= Ap;
+          }
+          s_am[5 * ROT_STAGE + t0 + lane] = Am;
         }
         __syncthreads();
         for (int k = warp; k < nunit; k += NW) {
@@ -2917,17 +2937,15 @@ struct Engine {
             nbot = (t0 + 32 + lane < nsu) ? ldcg(colp + q + rb + t0 + 33 + lane) : 0.0;
             double cs = 1.0, sn = 0.0;
             if (lane < cnt) { cs = s_c[t0 + lane]; sn = s_s[t0 + lane]; }
-            double Am = (lane < cnt) ? -sn : 1.0, Bm = (lane < cnt) ? cs * bot : 0.0;
+            // lanes past cnt may hold other rotations' products: no lane
+            // below cnt reads them
+            double Bm = (lane < cnt) ? cs * bot : 0.0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const double Ap = __shfl_up_sync(0xffffffffu, Am, o);
-              const double Bp = __shfl_up_sync(0xffffffffu, Bm, o);
-              if (lane >= o) {
-                Bm = fma(Am, Bp, Bm);
-                Am = Am * Ap;
-              }
+            for (int lv = 0; lv < 5; ++lv) {
+              const double Bp = __shfl_up_sync(0xffffffffu, Bm, 1 << lv);
+              if (lane >= (1 << lv)) Bm = fma(s_am[lv * ROT_STAGE + t0 + lane], Bp, Bm);
             }
-            const double incl = fma(Am, carry, Bm);  // carry after rotation lane
+            const double incl = fma(s_am[5 * ROT_STAGE + t0 + lane], carry, Bm);  // carry after rotation lane
             double cin = __shfl_up_sync(0xffffffffu, incl, 1);
             if (lane == 0) cin = carry;
             if (lane < cnt) colp[q + rb + t0 + lane] = cs * cin + sn * bot;
