@@ -2613,6 +2613,12 @@ struct Engine {
     // 64 cycles on its SM sub-partition, so the per-rotation FP64 work on
     // the dependent chain is kept to two instructions.
     const int nblk = (nrot + DB - 1) / DB;
+    // the ranks the chain leaves free apply the rotations as they appear
+    // (when they are at least a quarter of the team and the log fits one
+    // shared-memory stage); otherwise every rank applies them afterwards
+    bool follow = false;
+    if constexpr (std::is_same<Team, GridTeam>::value)
+      follow = nrot > 0 && nrot <= ROT_STAGE && 4 * (tm.size - nblk) >= tm.size;
     double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
     __shared__ double s_ra[DB], s_rq[DB], s_rqa[DB];
     __shared__ int s_rk[DB], s_rid[DB];
@@ -2866,35 +2872,121 @@ struct Engine {
         }
       }
     }
+    if (follow && tm.rank >= nblk && !rotate_columns(q, np, nrot, nblk, true)) {
+      failed = true;
+      status = LHDM_ERR_TIMEOUT;
+      return false;
+    }
     if (!sync()) return false;
     phase(PH_ZROT);
     nP = np - 1;
-    // (ii) the same rotations on every Z column and on b, and on R's columns
-    // at positions q .. nP-1 (rows q .. p+1 of position p take rotations
-    // q .. p; the last one zeroes row p+1): one warp per column; the carry
-    // recurrence c' = -s c + cs * bot is affine, so each 32-row chunk is a
-    // warp-wide prefix scan of affine maps
-    {
-      double* s_c = dyn;
-      double* s_s = dyn + ROT_STAGE;
-      // the scan's multiplicative parts, the same for every column: per
-      // 32-rotation chunk, lane t's running product of -sin before each of
-      // the five levels (rows 0-4) and after the last (row 5)
-      double* s_am = dyn + 2 * ROT_STAGE;  // 6 x ROT_STAGE
-      int c0, c1;
-      split(I.n, tm.size, tm.rank, c0, c1);
-      const bool do_b = (tm.rank == tm.size - 1);
-      __shared__ int s_zl[CAND_LOCAL_MAX + 1];
-      __shared__ int s_nz;
-      if (tid == 0) s_nz = 0;
-      __syncthreads();
-      for (int c = c0 + tid; c < c1; c += NT)
-        if (ldcg(I.pos + c) < 0) s_zl[atomicAdd(&s_nz, 1)] = c;
-      __syncthreads();
-      const int nz = s_nz + (do_b ? 1 : 0);
-      int r0, r1;
-      split(nrot, tm.size, tm.rank, r0, r1);
-      const int nunit = nz + (r1 - r0);
+    if (!follow) rotate_columns(q, np, nrot, 0, false);
+    const bool ok = sync();
+    phase(PH_INNER);
+    return ok;
+  }
+
+  // (ii) of the downdate: the rotations on every Z column and on b, and on
+  // R's columns at positions q .. np-2 (rows q .. p+1 of position p take
+  // rotations q .. p; the last one zeroes row p+1): one warp per column; the
+  // carry recurrence c' = -s c + cs * bot is affine, so each 32-row chunk is
+  // a warp-wide prefix scan of affine maps.  Ranks r0 .. size-1 share the
+  // columns.  With `follow` (ranks the chain leaves free, all rotations in
+  // one shared-memory stage) the work runs while the chain is still
+  // generating: warp 0 stages each 32-rotation chunk of the log as it is
+  // published and the other warps follow it; an R column starts once its
+  // own chain block's rotations are out, when that block no longer reads it
+  // (the chain never reads W or b).
+  __device__ bool rotate_columns(int q, int np, int nrot, int r0rank, bool follow) {
+    static_assert(DB == 32, "a chain block's rotations are one 32-rotation chunk");
+    double* s_c = dyn;
+    double* s_s = dyn + ROT_STAGE;
+    // the scan's multiplicative parts, the same for every column: per
+    // 32-rotation chunk, lane t's running product of -sin before each of
+    // the five levels (rows 0-4) and after the last (row 5)
+    double* s_am = dyn + 2 * ROT_STAGE;  // 6 x ROT_STAGE
+    const int zr = tm.rank - r0rank, nzr = tm.size - r0rank;
+    int c0, c1;
+    split(I.n, nzr, zr, c0, c1);
+    const bool do_b = (zr == nzr - 1);
+    __shared__ int s_zl[CAND_LOCAL_MAX + 1];
+    __shared__ int s_nz, s_avail;
+    volatile int* avail = &s_avail;  // chunks staged (follow); -1: abandoned
+    if (tid == 0) {
+      s_nz = 0;
+      s_avail = 0;
+    }
+    __syncthreads();
+    for (int c = c0 + tid; c < c1; c += NT)
+      if (ldcg(I.pos + c) < 0) s_zl[atomicAdd(&s_nz, 1)] = c;
+    __syncthreads();
+    const int nz = s_nz + (do_b ? 1 : 0);
+    // R columns round-robin over the ranks (the last positions, which take
+    // the most rotations, land on different CTAs)
+    const int nr_own = (zr < nrot) ? (nrot - zr + nzr - 1) / nzr : 0;
+    const int nunit = nz + nr_own;
+    // the products for the chunk at stage offset t0 (one warp)
+    auto chunk_products = [&](int t0, int ns) {
+      const int cnt = min(32, ns - t0);
+      double Am = (lane < cnt) ? -s_s[t0 + lane] : 1.0;
+#pragma unroll
+      for (int lv = 0; lv < 5; ++lv) {
+        s_am[lv * ROT_STAGE + t0 + lane] = Am;
+        const double Ap = __shfl_up_sync(0xffffffffu, Am, 1 << lv);
+        if (lane >= (1 << lv)) Am *= Ap;
+      }
+      s_am[5 * ROT_STAGE + t0 + lane] = Am;
+    };
+    // rotations rb + t0 .. rb + t0 + cnt - 1 (stage offset t0) on one column
+    auto chunk_apply = [&](double* colp, int rb, int t0, int cnt, double bot, double& carry) {
+      double cs = 1.0, sn = 0.0;
+      if (lane < cnt) {
+        cs = s_c[t0 + lane];
+        sn = s_s[t0 + lane];
+      }
+      // lanes past cnt may hold other rotations' products: no lane below
+      // cnt reads them
+      double Bm = (lane < cnt) ? cs * bot : 0.0;
+#pragma unroll
+      for (int lv = 0; lv < 5; ++lv) {
+        const double Bp = __shfl_up_sync(0xffffffffu, Bm, 1 << lv);
+        if (lane >= (1 << lv)) Bm = fma(s_am[lv * ROT_STAGE + t0 + lane], Bp, Bm);
+      }
+      const double incl = fma(s_am[5 * ROT_STAGE + t0 + lane], carry, Bm);  // carry after rotation lane
+      double cin = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (lane == 0) cin = carry;
+      if (lane < cnt) colp[q + rb + t0 + lane] = cs * cin + sn * bot;
+      carry = __shfl_sync(0xffffffffu, incl, cnt - 1);
+    };
+    // unit k: its column, its rotation count from rb on, whether they end an
+    // R column's rotations
+    auto unit = [&](int k, int rb, int ns, double*& colp, int& nsu, bool& rlast) {
+      nsu = ns;
+      rlast = false;
+      if (k < nz) {
+        colp = (k < s_nz) ? Wcol(s_zl[k]) : I.bt;
+      } else {
+        const int pr = q + zr + (k - nz) * nzr;  // R column at position pr
+        colp = Rcol(ldcg(I.rslot + pr));
+        nsu = min(ns, pr - q + 1 - rb);
+        rlast = (rb + nsu == pr - q + 1);
+      }
+    };
+    // a column's last carry: zero below an R column's diagonal; for a Z
+    // column row np-1 joins the trailing part and its norm grows by that
+    // entry (an update, free of cancellation)
+    auto finish_unit = [&](int k, double* colp, int at, bool rlast, double carry, bool last) {
+      if (lane == 0) {
+        colp[at] = rlast ? 0.0 : carry;
+        if (last && k < s_nz) {
+          const int c = s_zl[k];
+          const double uo = ldcg(I.u + c);
+          I.u[c] = sqrt(fma(carry, carry, uo * uo));
+        }
+      }
+    };
+    bool ok = true;
+    if (!follow) {
       for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
         const int ns = min(ROT_STAGE, nrot - rb);
         __syncthreads();
@@ -2903,82 +2995,132 @@ struct Engine {
           s_s[e] = ldcg(I.rots + rb + e);
         }
         __syncthreads();
-        for (int t0 = warp * 32; t0 < ns; t0 += NW * 32) {
-          const int cnt = min(32, ns - t0);
-          double Am = (lane < cnt) ? -s_s[t0 + lane] : 1.0;
-#pragma unroll
-          for (int lv = 0; lv < 5; ++lv) {
-            s_am[lv * ROT_STAGE + t0 + lane] = Am;
-            const double Ap = __shfl_up_sync(0xffffffffu, Am, 1 << lv);
-            if (lane >= (1 << lv)) Am *= Ap;
-          }
-          s_am[5 * ROT_STAGE + t0 + lane] = Am;
-        }
+        for (int t0 = warp * 32; t0 < ns; t0 += NW * 32) chunk_products(t0, ns);
         __syncthreads();
         for (int k = warp; k < nunit; k += NW) {
           double* colp;
-          int nsu = ns;
-          bool rlast = false;  // this chunk ends an R column's rotations
-          if (k < nz) {
-            colp = (k < s_nz) ? Wcol(s_zl[k]) : I.bt;
-          } else {
-            const int pr = q + r0 + (k - nz);  // R column at position pr
-            colp = Rcol(ldcg(I.rslot + pr));
-            nsu = min(ns, pr - q + 1 - rb);
-            if (nsu <= 0) continue;
-            rlast = (rb + nsu == pr - q + 1);
-          }
+          int nsu;
+          bool rlast;
+          unit(k, rb, ns, colp, nsu, rlast);
+          if (nsu <= 0) continue;
           double carry = ldcg(colp + q + rb);
           // next chunk's column values are loaded before the scan of this one
           double nbot = (lane < nsu) ? ldcg(colp + q + rb + 1 + lane) : 0.0;
           for (int t0 = 0; t0 < nsu; t0 += 32) {
-            const int cnt = min(32, nsu - t0);
             const double bot = nbot;
             nbot = (t0 + 32 + lane < nsu) ? ldcg(colp + q + rb + t0 + 33 + lane) : 0.0;
-            double cs = 1.0, sn = 0.0;
-            if (lane < cnt) { cs = s_c[t0 + lane]; sn = s_s[t0 + lane]; }
-            // lanes past cnt may hold other rotations' products: no lane
-            // below cnt reads them
-            double Bm = (lane < cnt) ? cs * bot : 0.0;
-#pragma unroll
-            for (int lv = 0; lv < 5; ++lv) {
-              const double Bp = __shfl_up_sync(0xffffffffu, Bm, 1 << lv);
-              if (lane >= (1 << lv)) Bm = fma(s_am[lv * ROT_STAGE + t0 + lane], Bp, Bm);
-            }
-            const double incl = fma(s_am[5 * ROT_STAGE + t0 + lane], carry, Bm);  // carry after rotation lane
-            double cin = __shfl_up_sync(0xffffffffu, incl, 1);
-            if (lane == 0) cin = carry;
-            if (lane < cnt) colp[q + rb + t0 + lane] = cs * cin + sn * bot;
-            carry = __shfl_sync(0xffffffffu, incl, cnt - 1);
+            chunk_apply(colp, rb, t0, min(32, nsu - t0), bot, carry);
           }
-          // an R column's last rotation zeroes the entry below its diagonal
-          if (lane == 0) colp[q + rb + nsu] = rlast ? 0.0 : carry;
-          // row nP (the last carry) joins a Z column's trailing part: its
-          // norm grows by that entry (an update, free of cancellation)
-          if (lane == 0 && k < s_nz && rb + ns == nrot) {
-            const int c = s_zl[k];
-            const double uo = ldcg(I.u + c);
-            I.u[c] = sqrt(fma(carry, carry, uo * uo));
-          }
+          finish_unit(k, colp, q + rb + nsu, rlast, carry, rb + ns == nrot);
         }
       }
       if (nrot == 0) {
-        // the last position went: row nP joins the trailing part unrotated
+        // the last position went: row np-1 joins the trailing part unrotated
         for (int k = tid; k < s_nz; k += NT) {
           const int c = s_zl[k];
-          const double v = ldcg(Wcol(c) + nP), uo = ldcg(I.u + c);
+          const double v = ldcg(Wcol(c) + np - 1), uo = ldcg(I.u + c);
           I.u[c] = sqrt(fma(v, v, uo * uo));
         }
       }
-      // the triangular solve that follows reads rhs = (Q^T b)[0:nP]
-      if (do_b) {
-        __syncthreads();
-        for (int p = tid; p < nP; p += NT) I.rhs[p] = ldcg(I.bt + p);
+    } else if (warp == 0) {
+      // stage the log chunk by chunk as it is published (every slot holds
+      // NaN until its rotation is written)
+      const int nch = (nrot + 31) / 32;
+      const long long tw0 = gtimer();
+      unsigned spins = 0;
+      for (int ch = 0; ch < nch && ok; ++ch) {
+        const int t = ch * 32 + lane;
+        const bool in = t < nrot;
+        double cv = 1.0, sv = 0.0;
+        for (;;) {
+          if (in) {
+            cv = *(volatile const double*)(I.rotc + t);
+            sv = *(volatile const double*)(I.rots + t);
+          }
+          if (__ballot_sync(0xffffffffu, in && (isnan(cv) || isnan(sv))) == 0u) break;
+          __nanosleep(200);  // the generating CTAs poll the same lines
+          if ((++spins & 63u) == 0u) {
+            int bad = 0;
+            if (lane == 0) {
+              int* er = tm_err();
+              bad = (er && *(volatile int*)er) ? 1 : 0;
+              if (!bad && gtimer() - tw0 > I.wait_ns) {
+                if (er) atomicExch(er, 1);
+                bad = 1;
+              }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) {
+              ok = false;
+              break;
+            }
+          }
+        }
+        if (!ok) break;
+        if (in) {
+          s_c[t] = cv;
+          s_s[t] = sv;
+        }
+        __syncwarp();
+        chunk_products(ch * 32, nrot);
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *avail = ch + 1;
+      }
+      if (!ok && lane == 0) *avail = -1;
+    } else {
+      // wait until n chunks are staged (false: abandoned or timed out)
+      auto wait_avail = [&](int n) {
+        int st = 0;
+        if (lane == 0) {
+          const long long tw0 = gtimer();
+          unsigned spins = 0;
+          for (;;) {
+            const int a = *avail;
+            if (a < 0) { st = 0; break; }
+            if (a >= n) { st = 1; break; }
+            if ((++spins & 63u) == 0u && gtimer() - tw0 > I.wait_ns) {
+              int* er = tm_err();
+              if (er) atomicExch(er, 1);
+              st = 0;
+              break;
+            }
+          }
+        }
+        st = __shfl_sync(0xffffffffu, st, 0);
+        __threadfence_block();
+        return st != 0;
+      };
+      for (int k = warp - 1; k < nunit && ok; k += NW - 1) {
+        double* colp;
+        int nsu;
+        bool rlast;
+        unit(k, 0, nrot, colp, nsu, rlast);
+        // an R column waits for its own chain block's rotations: that block
+        // read the column from global memory before generating them
+        if (k >= nz && !wait_avail((nsu - 1) / DB + 1)) {
+          ok = false;
+          break;
+        }
+        double carry = ldcg(colp + q);
+        double nbot = (lane < nsu) ? ldcg(colp + q + 1 + lane) : 0.0;
+        for (int t0 = 0; t0 < nsu; t0 += 32) {
+          if (!wait_avail(t0 / 32 + 1)) {
+            ok = false;
+            break;
+          }
+          const double bot = nbot;
+          nbot = (t0 + 32 + lane < nsu) ? ldcg(colp + q + t0 + 33 + lane) : 0.0;
+          chunk_apply(colp, 0, t0, min(32, nsu - t0), bot, carry);
+        }
+        if (!ok) break;
+        finish_unit(k, colp, q + nsu, rlast, carry, true);
       }
     }
-    const bool ok = sync();
-    phase(PH_INNER);
-    return ok;
+    // the triangular solve that follows reads rhs = (Q^T b)[0:np-1]
+    if (__syncthreads_or(!ok)) return false;
+    if (do_b)
+      for (int p = tid; p < np - 1; p += NT) I.rhs[p] = ldcg(I.bt + p);
+    return true;
   }
 
   __device__ int* tm_err();
