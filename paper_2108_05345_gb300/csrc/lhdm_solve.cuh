@@ -345,15 +345,34 @@ struct Engine {
     __shared__ int s_off[1024 + 1];
     __shared__ int s_kc;
     {
-      // prefix offsets of the per-CTA lists (team size <= 1024)
-      if (tid == 0) {
-        int acc = 0;
-        for (int t = 0; t < tm.size; ++t) {
-          s_off[t] = acc;
-          acc += ldcg(I.candn + t);
+      // prefix offsets of the per-CTA lists (team size <= 1024): the counts
+      // are loaded at once (one L2 round trip), then a warp-wide scan
+      if (warp == 0) {
+        int run = 0;
+        for (int j0 = 0; j0 * 32 < tm.size; j0 += 8) {
+          int cntv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int t = (j0 + j) * 32 + lane;
+            cntv[j] = (t < tm.size) ? ldcg(I.candn + t) : 0;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            int inc = cntv[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, inc, o);
+              if (lane >= o) inc += y;
+            }
+            const int t = (j0 + j) * 32 + lane;
+            if (t < tm.size) s_off[t] = run + inc - cntv[j];
+            run += __shfl_sync(0xffffffffu, inc, 31);
+          }
         }
-        s_off[tm.size] = acc;
-        s_kc = min(acc, kc_max);
+        if (lane == 0) {
+          s_off[tm.size] = run;
+          s_kc = min(run, kc_max);
+        }
       }
       __syncthreads();
       const int total = s_off[tm.size];
@@ -465,15 +484,16 @@ struct Engine {
       __shared__ double s_d[KM];
       __shared__ unsigned long long s_mask[KM];
       if (tid < KK) {
-        s_d[tid] = sqrt(ldcg(I.Gm + tid * KM + tid));
+        s_d[tid] = sqrt_gm(ldcg(I.Gm + tid * KM + tid));
         s_mask[tid] = 0ull;
       }
       __syncthreads();
+      // |theta_al| = |G_al| / (d_a d_l) < delta, tested without the division
+      // (d > 0: every candidate is eligible, u_j > 100 eps ||a_j||)
       for (int p = tid; p < KK * KK; p += NT) {
         const int a = p / KK, l = p - a * KK;
         if (l >= a) continue;
-        const double theta = ldcg(I.Gm + a * KM + l) / (s_d[a] * s_d[l]);
-        if (fabs(theta) < I.prm.delta) atomicOr(&s_mask[a], 1ull << l);
+        if (fabs(ldcg(I.Gm + a * KM + l)) < I.prm.delta * (s_d[a] * s_d[l])) atomicOr(&s_mask[a], 1ull << l);
       }
       __syncthreads();
       __shared__ int s_sel[KM];
