@@ -2639,7 +2639,8 @@ struct Engine {
     bool follow = false;
     if constexpr (std::is_same<Team, GridTeam>::value)
       follow = nrot > 0 && nrot <= ROT_STAGE && 4 * (tm.size - nblk) >= tm.size;
-    double* sB = dyn;  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
+    double* sB = dyn;                  // sB[e][l] = R(bs+1+e, position bs+l), DB x (DB+1)
+    double* sY = dyn + DB * (DB + 1);  // -sB[e][l] / sB[e][e] (the one-FMA form below)
     __shared__ double s_ra[DB], s_rq[DB], s_rqa[DB];
     __shared__ int s_rk[DB], s_rid[DB];
     __shared__ int s_prog, s_qprog;  // rotations generated / with their scale (-1: abandoned)
@@ -2663,11 +2664,33 @@ struct Engine {
         *qprog = 0;
       }
       __syncthreads();
+      for (int idx = tid; idx < DB * DB; idx += NT) {
+        const int e = idx / DB, l = idx - e * DB;
+        const double be = sB[e * (DB + 1) + e];
+        sY[e * (DB + 1) + l] = (be != 0.0) ? -sB[e * (DB + 1) + l] * rcp_nr(be) : 0.0;
+      }
+      __syncthreads();
       if (warp == 0) {
         const int pl = bs + lane;
         const bool act = pl < np - 1;
         const double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
         double carry = act ? ldcg(col + q) : 0.0;
+        // the one-FMA form of the block's own steps (below) when every b_e
+        // is nonzero and within 2^+-24 (the products of 32 of them stay far
+        // inside the FP64 range): Dx = prod_{i < lane} (-b_i)
+        const double bme = (lane < nown) ? sB[lane * (DB + 1) + lane] : 1.0;
+        const bool fast = __all_sync(0xffffffffu, lane >= nown || (bme != 0.0 && abs(ebound(bme)) < 24));
+        double Dx = 1.0;
+        if (fast) {
+          double Di = (lane < nown) ? -bme : 1.0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const double tt = __shfl_up_sync(0xffffffffu, Di, o);
+            if (lane >= o) Di *= tt;
+          }
+          Dx = __shfl_up_sync(0xffffffffu, Di, 1);
+          if (lane == 0) Dx = 1.0;
+        }
         // earlier blocks' rotations, as they appear in the log, up to 16 at
         // a time (lanes 0-15 poll cosines, 16-31 sines); the column values
         // are loaded before the wait.  carry = row t of this column after
@@ -2731,7 +2754,46 @@ struct Engine {
         // a~, the zero-radius flags and the exponent go to the publisher.
         constexpr int RG = 8;
         double xt = carry;
-        for (int e0 = 0; e0 < nown; e0 += RG) {
+        // One-FMA form: with D_e = prod_{i < e} (-b_i), z_l = xt_l / D_e
+        // moves as z_l += z_e Y~(e, l), Y~ = -y / b: one FP64 instruction
+        // per step instead of two.  At a group's end a~ = z D of the lane's
+        // own step, and the lanes still to come go on at scale D_{el+1}
+        // (their xt = z D_{el+1} decides the renormalisation, applied to z
+        // as to xt).  No zero radius can occur (b != 0).
+        for (int e0 = 0; fast && e0 < nown; e0 += RG) {
+          double yg[RG];
+#pragma unroll
+          for (int jj = 0; jj < RG; ++jj) yg[jj] = sY[min(e0 + jj, DB - 1) * (DB + 1) + lane];
+#pragma unroll
+          for (int jj = 0; jj < RG; ++jj) {
+            const int e = e0 + jj;
+            if (e < nown) {
+              const double a = __shfl_sync(0xffffffffu, xt, e);
+              if (lane > e) xt = fma(a, yg[jj], xt);
+            }
+          }
+          const int el = min(e0 + RG, nown) - 1;
+          const bool mine = lane >= e0 && lane <= el;
+          const double Dn = __shfl_sync(0xffffffffu, Dx, min(el + 1, DB - 1));
+          const double xs = xt * (lane <= el ? Dx : Dn);  // a~ (mine), or xt at scale D_{el+1}
+          if (mine) {
+            s_ra[lane] = xs;
+            s_rid[lane] = 0;
+          }
+          int ex = (act && lane > el) ? (int)((__double_as_longlong(xs) >> 52) & 0x7ff) : 0;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+          int k = 0;
+          if (ex > 1023 + 128 || (ex > 0 && ex < 1023 - 128)) {
+            k = ex - 1023;
+            if (lane > el) xt = ldexp(xt, -k);
+          }
+          if (mine) s_rk[lane] = (lane == el) ? k : 0;
+          __threadfence_block();
+          if (lane == 0) *prog = el + 1;
+          __syncwarp();
+        }
+        for (int e0 = 0; !fast && e0 < nown; e0 += RG) {
           double bg[RG], yg[RG];
 #pragma unroll
           for (int jj = 0; jj < RG; ++jj) {
