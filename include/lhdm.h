@@ -323,12 +323,12 @@ int lhdm_debug_commit_guard(lhdm_ctx* ctx, int32_t mode);
 int lhdm_debug_stall_next_solve(lhdm_ctx* ctx);
 
 /*
- * Verification aid for the reciprocal and square root the panel's scalar
+ * Verification aid for the reciprocal and square root the solver's scalar
  * chains use in place of the compiler's correctly rounded ones (Newton-
  * Raphson from a single-precision seed; Goldschmidt with a Newton
  * correction).  For each of the n device doubles x[i], out (device, 4 n
- * doubles) receives out[4i] = the panel's 1/x, out[4i+1] = 1.0/x,
- * out[4i+2] = the panel's sqrt(|x|), out[4i+3] = sqrt(|x|), computed on the
+ * doubles) receives out[4i] = the solver's 1/x, out[4i+1] = 1.0/x,
+ * out[4i+2] = the solver's sqrt(|x|), out[4i+3] = sqrt(|x|), computed on the
  * device on `stream`; the call does not synchronise.
  * Errors: INVALID_ARG (n < 0, or a null pointer with n > 0), CUDA.
  */

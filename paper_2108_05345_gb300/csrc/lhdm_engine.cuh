@@ -391,7 +391,9 @@ __device__ __forceinline__ double ll_scaled(long long u, int es) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-// Reciprocal and square root for the scalar chains of the panel.  On this
+// Reciprocal and square root for the solver's scalar chains (the panel's
+// reflectors, the diagonal reciprocals of the triangular solves, the
+// rotation publisher of the downdate).  On this
 // GPU one FP64 instruction is 64 cycles of a sub-partition, and the
 // correctly rounded division and square root of the compiler take about ten
 // each; these take four and five on the dependent path.  The seed is the

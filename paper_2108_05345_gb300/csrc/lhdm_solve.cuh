@@ -1083,8 +1083,8 @@ struct Engine {
     double a0 = (lane < k) ? ldcg(I.pr + lane) : 0.0;
     double a1 = (lane + 32 < k) ? ldcg(I.pr + lane + 32) : 0.0;
     // reciprocal diagonal computed by all lanes at once, off the chain
-    const double r0 = (lane < k) ? 1.0 / ldcg(I.R22 + lane + lane * KM) : 0.0;
-    const double r1 = (lane + 32 < k) ? 1.0 / ldcg(I.R22 + (lane + 32) + (lane + 32) * KM) : 0.0;
+    const double r0 = (lane < k) ? rcp_nr(ldcg(I.R22 + lane + lane * KM)) : 0.0;
+    const double r1 = (lane + 32 < k) ? rcp_nr(ldcg(I.R22 + (lane + 32) + (lane + 32) * KM)) : 0.0;
     double y0 = 0.0, y1 = 0.0;
     for (int jj = k - 1; jj >= 0; --jj) {
       const int owner = jj & 31;
@@ -1194,7 +1194,7 @@ struct Engine {
           for (int q2 = 0; q2 < TB * TB / NT; ++q2) {
             const int idx = tid + q2 * NT, cl = idx / TB, rw = idx - cl * TB;
             sD[cl * (TB + 1) + rw] = v[q2];
-            if (rw == cl && cl < nbk) s_rinv[cl] = 1.0 / v[q2];
+            if (rw == cl && cl < nbk) s_rinv[cl] = rcp_nr(v[q2]);
           }
         }
         if (has_next) {
@@ -1363,7 +1363,7 @@ struct Engine {
           const int idx = tid + k * NT, j = v + idx / TB, i = idx & (TB - 1);
           if (idx < ns) {
             sD[j * (TB + 1) + i] = sv[k];
-            if (i == j) s_rinv[j] = 1.0 / sv[k];
+            if (i == j) s_rinv[j] = rcp_nr(sv[k]);
           }
         }
       }
@@ -1522,7 +1522,7 @@ struct Engine {
         for (int k = 0; k < TB * TB / NT; ++k) {
           const int idx = tid + k * NT, j = idx / TB, i = idx & (TB - 1);
           sD[j * (TB + 1) + i] = sv[k];
-          if (i == j && j < nbk) s_ri[j] = 1.0 / sv[k];
+          if (i == j && j < nbk) s_ri[j] = rcp_nr(sv[k]);
         }
       }
       __syncthreads();
@@ -2935,7 +2935,7 @@ struct Engine {
               const double a = s_ra[k], bk = sB[k * (DB + 1) + k], qk = s_rq[k], qa = s_rqa[k];
               const bool idr = s_rid[k] != 0;
               const double iqa = idr ? 0.0 : rsqrt(qa);
-              I.rots[bs - q + k] = idr ? 0.0 : bk * sqrt(qk) * iqa;
+              I.rots[bs - q + k] = idr ? 0.0 : bk * sqrt_gm(qk) * iqa;
               I.rotc[bs - q + k] = idr ? 1.0 : a * iqa;
             }
             done = pg;

@@ -170,7 +170,7 @@ def solve_noalloc(A, b, params=None, x=None, passive=None, info=None, stream=Non
 
 def fast_math(x, stream=None):
     """lhdm_debug_fast_math on a CUDA float64 tensor x: an (n, 4) tensor of
-    (panel 1/x, 1.0/x, panel sqrt|x|, sqrt|x|)."""
+    (solver 1/x, 1.0/x, solver sqrt|x|, sqrt|x|)."""
     import torch
     x = x.contiguous()
     out = torch.empty((x.numel(), 4), dtype=torch.float64, device=x.device)

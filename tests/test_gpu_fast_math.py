@@ -1,4 +1,4 @@
-"""The panel's reciprocal (Newton-Raphson from a single-precision seed) and
+"""The solver's reciprocal (Newton-Raphson from a single-precision seed) and
 square root (Goldschmidt step plus a Newton correction with the exact
 remainder) against the library's correctly rounded division and square root
 on the GPU: within one ulp over the normal range (both signs, mantissas and
