@@ -101,10 +101,14 @@ struct Engine {
 
   // Flags of the pipelined solve start at zero in every launch (a barrier
   // must follow before the first solve).
+  // A slab sum of the pipelined triangular solve not yet written: a NaN
+  // payload no arithmetic produces (results carry the canonical quiet NaN).
+  static constexpr long long ACC_EMPTY = 0x7ff4dead0000beefLL;
   __device__ void clear_tri_flags() {
     if (!I.tflag) return;
     const int nbk = (I.cap + TB - 1) / TB, nfl = nbk * (1 + TB / SLAB + INV_PARTS);
     for (int i = tm.rank * NT + tid; i < nfl; i += tm.size * NT) I.tflag[i] = 0;
+    for (int i = tm.rank * NT + tid; i < nbk * TB; i += tm.size * NT) I.accb[i] = __longlong_as_double(ACC_EMPTY);
   }
 
   // ------------------------------------------------------------ setup
@@ -1301,9 +1305,9 @@ struct Engine {
     __shared__ int s_slot[2][TB];           // slots of block bi in s_slot[bi & 1]
     const int row = tid & (TB - 1), g = tid >> 6;  // 8 groups of 8 columns
     int* yfl = yflags();
-    const int* sfl = sflags();
     const int* ifl = iflags();
     int pslot = 0;
+    double pacc = 0.0;  // the block's slab sum as last seen (ACC_EMPTY: not yet written)
     auto valid_cols = [&](int b0, int nbk) { return min(max(inv_valid - b0, 0), nbk); };
     // block bi's loads that wait for nothing (its columns' slots are those
     // of block bi + 1, already in s_slot)
@@ -1322,6 +1326,7 @@ struct Engine {
       }
       if (g == 0) cp8(s_rh + row, row < nbk ? I.rhs + b0 + row : I.rhs, row < nbk);
       cp_commit();
+      if (g == 0 && row < nbk && bi + 2 < nb) pacc = ldcg(I.accb + b0 + row);
     };
     prefetch(nb - 1);
     for (int bi = nb - 1; bi >= 0; --bi) {
@@ -1377,12 +1382,30 @@ struct Engine {
         }
         sP[g * TB + row] = p0 + p1;
       }
-      // slab accumulations of blocks b+2, ...
+      // slab accumulations of blocks b+2, ...: the value is its own flag
+      // (written once per solve, 8-byte single-copy atomic), usually already
+      // there when the block before this one read it ahead
       int okw = 1;
       double acc = 0.0;
       if (g == 0 && row < nbk && bi + 2 < nb) {
-        okw = wait_ge(sfl + (b0 + row) / SLAB, ep, tm_err(), I.wait_ns) ? 1 : 0;
-        if (okw) acc = ldcg(I.accb + b0 + row);
+        acc = pacc;
+        if (__double_as_longlong(acc) == ACC_EMPTY) {
+          const long long tw0 = gtimer();
+          unsigned spins = 0;
+          for (;;) {
+            acc = *(volatile const double*)(I.accb + b0 + row);
+            if (__double_as_longlong(acc) != ACC_EMPTY) break;
+            if ((++spins & 63u) == 0u) {
+              int* er = tm_err();
+              if ((er && *(volatile int*)er) || gtimer() - tw0 > I.wait_ns) {
+                if (er) atomicExch(er, 1);
+                okw = 0;
+                break;
+              }
+            }
+          }
+        }
+        I.accb[b0 + row] = __longlong_as_double(ACC_EMPTY);  // empty again for the next solve
       }
       if (!__syncthreads_and(okw)) return false;
       if (g == 0 && row < nbk) {
@@ -1457,7 +1480,6 @@ struct Engine {
     double* s_red = dyn;                  // (NT / SLAB) x SLAB
     const int row = tid & (SLAB - 1), cg = tid / SLAB;   // cg in [0, 32)
     const int* yfl = yflags();
-    int* sfl = sflags();
     for (int s = h + nh * ((nslab - 1 - h) / nh); s >= 0; s -= nh) {
       const int rb = s / SPB, r0 = s * SLAB;
       double acc = 0.0;
@@ -1480,10 +1502,9 @@ struct Engine {
       __syncthreads();
       if (warp < SLAB) {
         const double t = warp_sum(s_red[lane * SLAB + warp]);
-        if (lane == 0) I.accb[r0 + warp] = t;
+        if (lane == 0) I.accb[r0 + warp] = t;  // read by rank 0 as its own flag
       }
       __syncthreads();
-      if (tid == 0) flag_release(sfl + s, ep);
     }
     return true;
   }
