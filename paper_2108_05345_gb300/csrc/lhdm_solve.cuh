@@ -384,36 +384,51 @@ struct Engine {
       split(total, tm.size, tm.rank, e0, e1);
       unsigned long long* s_k = reinterpret_cast<unsigned long long*>(dyn);
       int* s_c = reinterpret_cast<int*>(s_k + CAND_STAGE);
-      // my elements (at most ~total/size), ranks accumulated over staged passes
-      const int mine = e1 - e0;
-      int my_rank = 0;
-      unsigned long long my_key = 0;
-      int my_c = -1;
-      const int e = e0 + tid;
-      if (tid < mine) {
-        int t = 0;
-        while (s_off[t + 1] <= e) ++t;
-        const int q = e - s_off[t];
-        my_key = wkey(ldcg(I.candw + (size_t)t * KM + q));
-        my_c = ldcg(I.candi + (size_t)t * KM + q);
-      }
-      for (int base = 0; base < total; base += CAND_STAGE) {
-        const int nst = min(CAND_STAGE, total - base);
-        __syncthreads();
-        for (int k = tid; k < nst; k += NT) {
-          const int g = base + k;
-          int t = 0;
-          // lists are short; linear search over the offsets
-          while (s_off[t + 1] <= g) ++t;
-          const int q = g - s_off[t];
-          s_k[k] = wkey(ldcg(I.candw + (size_t)t * KM + q));
-          s_c[k] = ldcg(I.candi + (size_t)t * KM + q);
+      // the list and position of merged candidate g (binary search of the
+      // offsets)
+      auto locate = [&](int g, int& t, int& q) {
+        int lo = 0, hi = tm.size;  // s_off[lo] <= g < s_off[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_off[mid] <= g) lo = mid;
+          else hi = mid;
         }
-        __syncthreads();
-        if (tid < mine)
-          for (int k = 0; k < nst; ++k) my_rank += better(s_k[k], s_c[k], my_key, my_c);
+        t = lo;
+        q = g - s_off[lo];
+      };
+      // my elements (about total / size): a group of 16 threads per element
+      // counts the better candidates, each thread a 16th of them, over the
+      // staged passes; the counts are added in the group at the end
+      const int mine = e1 - e0;
+      const int grp = tid >> 4, sub = tid & 15;
+      for (int eb = 0; eb < mine; eb += NT / 16) {
+        const int me = eb + grp;
+        unsigned long long my_key = 0;
+        int my_c = -1;
+        if (me < mine) {
+          int t, q;
+          locate(e0 + me, t, q);
+          my_key = wkey(ldcg(I.candw + (size_t)t * KM + q));
+          my_c = ldcg(I.candi + (size_t)t * KM + q);
+        }
+        int cnt = 0;
+        for (int base = 0; base < total; base += CAND_STAGE) {
+          const int nst = min(CAND_STAGE, total - base);
+          __syncthreads();
+          for (int k = tid; k < nst; k += NT) {
+            int t, q;
+            locate(base + k, t, q);
+            s_k[k] = wkey(ldcg(I.candw + (size_t)t * KM + q));
+            s_c[k] = ldcg(I.candi + (size_t)t * KM + q);
+          }
+          __syncthreads();
+          if (me < mine)
+            for (int k = sub; k < nst; k += 16) cnt += better(s_k[k], s_c[k], my_key, my_c);
+        }
+#pragma unroll
+        for (int o = 8; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (me < mine && sub == 0 && cnt < kc_max) I.J[1 + cnt] = my_c;
       }
-      if (tid < mine && my_rank < kc_max) I.J[1 + my_rank] = my_c;
       if (tm.rank == 0 && tid == 0) I.J[0] = jsel;
     }
     if (!sync()) return false;
