@@ -452,9 +452,10 @@ __device__ __forceinline__ double fx_x(long long q, int E) { return scale2((doub
 
 // ---------------------------------------------------------------- teams
 // Whole-grid team: one CTA per SM, co-resident (cooperative launch).  The
-// barrier is a generation counter; every wait is bounded by wait_ns and sets
-// *err on expiry, after which every CTA leaves the solve.  `extra` raises the
-// arrival count of the main barrier beyond the grid: only the
+// barrier counts arrivals on a word that only grows (see arrive_wait); every
+// wait is bounded by wait_ns and sets *err on expiry, after which every CTA
+// leaves the solve.  `extra` raises the arrival count of the main barrier
+// beyond the grid: only the
 // failure-detection test sets it, so that no CTA ever releases the barrier and
 // every wait runs out.
 struct GridTeam {
