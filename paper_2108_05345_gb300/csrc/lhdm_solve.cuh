@@ -3104,7 +3104,76 @@ struct Engine {
       }
     };
     bool ok = true;
-    if (!follow) {
+    bool lanes = false;
+    if constexpr (std::is_same<Team, CtaTeam>::value) lanes = nrot > 0 && nrot <= ROT_STAGE;
+    if (lanes) {
+      // One CTA holds every column, so a lane can take a whole column: the
+      // recurrence runs down the rows one rotation at a time, four FP64
+      // instructions per 32 columns and rotation against the scan's nine
+      // per 32 rows of one column.  Columns go in groups of 32 per warp (Z
+      // columns and b first, then R's, whose rotation counts grow by one per
+      // position); 16-rotation row tiles of the group are staged in shared
+      // memory with coalesced loads (a column's 16 rows per half-warp) and
+      // written back the same way.
+      constexpr int TR = 16;
+      double* sT = dyn + 2 * ROT_STAGE + warp * (TR * 33);
+      __syncthreads();
+      for (int e = tid; e < nrot; e += NT) {
+        s_c[e] = ldcg(I.rotc + e);
+        s_s[e] = ldcg(I.rots + e);
+      }
+      __syncthreads();
+      const int ncol = nz + nrot;
+      for (int g = warp; g * 32 < ncol; g += NW) {
+        const int k = g * 32 + lane;
+        double* colp = I.bt;
+        int nsu = 0;
+        bool rlast = false;
+        if (k < ncol) unit(k, 0, nrot, colp, nsu, rlast);
+        double carry = (nsu > 0) ? ldcg(colp + q) : 0.0;
+        int gmax = nsu;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        const int hl = lane >> 4, il = lane & 15;
+        for (int t0 = 0; t0 < gmax; t0 += TR) {
+          // rows q+t0+1 .. q+t0+TR (the bots of rotations t0 ..)
+          for (int cc = 0; cc < 32; cc += 2) {
+            const int c = cc + hl;
+            const double* cp = reinterpret_cast<const double*>(__shfl_sync(0xffffffffu, reinterpret_cast<long long>(colp), c));
+            const int ns_c = __shfl_sync(0xffffffffu, nsu, c);
+            sT[il * 33 + c] = (t0 + il < ns_c) ? ldcg(cp + q + t0 + 1 + il) : 0.0;
+          }
+          __syncwarp();
+#pragma unroll 4
+          for (int i = 0; i < TR; ++i) {
+            const int t = t0 + i;
+            if (t < nsu) {
+              const double cs = s_c[t], sn = s_s[t], bot = sT[i * 33 + lane];
+              const double out = fma(sn, bot, cs * carry);
+              carry = fma(cs, bot, -sn * carry);
+              sT[i * 33 + lane] = out;
+            }
+          }
+          __syncwarp();
+          // outputs of rotations t0 .. go to rows q+t0 ..
+          for (int cc = 0; cc < 32; cc += 2) {
+            const int c = cc + hl;
+            double* cp = reinterpret_cast<double*>(__shfl_sync(0xffffffffu, reinterpret_cast<long long>(colp), c));
+            const int ns_c = __shfl_sync(0xffffffffu, nsu, c);
+            if (t0 + il < ns_c) cp[q + t0 + il] = sT[il * 33 + c];
+          }
+          __syncwarp();
+        }
+        if (nsu > 0) {
+          colp[q + nsu] = rlast ? 0.0 : carry;
+          if (k < s_nz) {
+            const int c = s_zl[k];
+            const double uo = ldcg(I.u + c);
+            I.u[c] = sqrt(fma(carry, carry, uo * uo));
+          }
+        }
+      }
+    } else if (!follow) {
       for (int rb = 0; rb < nrot; rb += ROT_STAGE) {
         const int ns = min(ROT_STAGE, nrot - rb);
         __syncthreads();
