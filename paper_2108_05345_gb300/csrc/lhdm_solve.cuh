@@ -1184,15 +1184,33 @@ struct Engine {
       }
       __syncthreads();
       if (has_next) {
-        // rows [0, b0): contribution of block bi+1, one warp per row (lanes
-        // over the block's columns: all loads independent), rows spread
-        // over the team
-        const int gw = tm.rank * NW + warp, nwt = tm.size * NW;
-        for (int row = gw; row < b0; row += nwt) {
-          const double p0 = (lane < nc) ? ldcg(Rcol(s_slot[lane]) + row) * s_y[lane] : 0.0;
-          const double p1 = (lane + 32 < nc) ? ldcg(Rcol(s_slot[lane + 32]) + row) * s_y[lane + 32] : 0.0;
-          const double sacc = warp_sum(p0 + p1);
-          if (lane == 0) I.rhs[row] = ldcg(I.rhs + row) - sacc;
+        if constexpr (std::is_same<Team, CtaTeam>::value) {
+          // one CTA: a thread per row, over the block's columns (loads of a
+          // column coalesced across the rows; no cross-lane sums, which cost
+          // five FP64 instructions per row and warp)
+          for (int row = tid; row < b0; row += NT) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = 0;
+            for (; j + 3 < nc; j += 4) {
+              a0 = fma(ldcg(Rcol(s_slot[j]) + row), s_y[j], a0);
+              a1 = fma(ldcg(Rcol(s_slot[j + 1]) + row), s_y[j + 1], a1);
+              a2 = fma(ldcg(Rcol(s_slot[j + 2]) + row), s_y[j + 2], a2);
+              a3 = fma(ldcg(Rcol(s_slot[j + 3]) + row), s_y[j + 3], a3);
+            }
+            for (; j < nc; ++j) a0 = fma(ldcg(Rcol(s_slot[j]) + row), s_y[j], a0);
+            I.rhs[row] = ldcg(I.rhs + row) - ((a0 + a1) + (a2 + a3));
+          }
+        } else {
+          // rows [0, b0): contribution of block bi+1, one warp per row
+          // (lanes over the block's columns: all loads independent), rows
+          // spread over the team
+          const int gw = tm.rank * NW + warp, nwt = tm.size * NW;
+          for (int row = gw; row < b0; row += nwt) {
+            const double p0 = (lane < nc) ? ldcg(Rcol(s_slot[lane]) + row) * s_y[lane] : 0.0;
+            const double p1 = (lane + 32 < nc) ? ldcg(Rcol(s_slot[lane + 32]) + row) * s_y[lane + 32] : 0.0;
+            const double sacc = warp_sum(p0 + p1);
+            if (lane == 0) I.rhs[row] = ldcg(I.rhs + row) - sacc;
+          }
         }
       }
       if (tm.rank == 0) {
