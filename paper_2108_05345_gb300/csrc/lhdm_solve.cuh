@@ -1251,6 +1251,14 @@ struct Engine {
           sP[g * TB + rw] = sacc;
         }
         __syncthreads();
+        // columns scaled by their reciprocal diagonal: the substitution below
+        // then needs no multiply on its chain (y_j = a_j / R_jj is formed for
+        // every row at the end)
+        for (int idx = tid; idx < TB * TB; idx += NT) {
+          const int cl = idx / TB, rw = idx - cl * TB;
+          if (cl < nbk && rw < cl) sD[cl * (TB + 1) + rw] *= s_rinv[cl];
+        }
+        __syncthreads();
         if (warp == 0) {
           double a0 = 0.0, a1 = 0.0;
           if (lane < nbk) {
@@ -1263,17 +1271,21 @@ struct Engine {
             if (has_next)
               for (int g = 0; g < 8; ++g) a1 -= sP[g * TB + lane + 32];
           }
-          for (int jj = nbk - 1; jj >= 0; --jj) {
-            const int owner = jj & 31;
-            const bool hi = jj >= 32;
+          // a_i -= (R_ij / R_jj) a_j, j from the last row up; rows 32 .. 63
+          // first (they feed both halves), then rows 0 .. 31 (one FMA a step)
+          for (int jj = nbk - 1; jj >= 32; --jj) {
             const double* cj = sD + jj * (TB + 1);
-            double yv = 0.0;
-            if (lane == owner) yv = (hi ? a1 : a0) * s_rinv[jj];
-            yv = __shfl_sync(0xffffffffu, yv, owner);
-            if (lane == owner) I.yP[b0 + jj] = yv;
-            if (lane < jj) a0 -= cj[lane] * yv;
-            if (lane + 32 < jj) a1 -= cj[lane + 32] * yv;
+            const double aj = __shfl_sync(0xffffffffu, a1, jj & 31);
+            a0 = fma(-cj[lane], aj, a0);
+            if (lane + 32 < jj) a1 = fma(-cj[lane + 32], aj, a1);
           }
+          for (int jj = min(nbk, 32) - 1; jj >= 0; --jj) {
+            const double* cj = sD + jj * (TB + 1);
+            const double aj = __shfl_sync(0xffffffffu, a0, jj);
+            if (lane < jj) a0 = fma(-cj[lane], aj, a0);
+          }
+          if (lane < nbk) I.yP[b0 + lane] = a0 * s_rinv[lane];
+          if (lane + 32 < nbk) I.yP[b0 + lane + 32] = a1 * s_rinv[lane + 32];
         }
       }
       if (!sync()) return false;
