@@ -2712,6 +2712,19 @@ struct Engine {
     __shared__ int s_prog, s_qprog;  // rotations generated / with their scale (-1: abandoned)
     volatile int* prog = &s_prog;
     volatile int* qprog = &s_qprog;
+    // A one-CTA team runs the blocks one after another, so it keeps every
+    // later position's running row value in shared memory and carries all
+    // of them through each block's rotations as soon as they are out, with
+    // every thread (one FP64 pipe per sub-partition) instead of the next
+    // block's warp 0 replaying the whole log on one.
+    double* s_car = dyn + 2 * DB * (DB + 1);
+    __shared__ double s_rc[DB], s_rs[DB];
+    bool car = false;
+    if constexpr (std::is_same<Team, CtaTeam>::value) car = nrot <= DYN_SMEM / 8 - 2 * DB * (DB + 1);
+    if (car) {
+      __syncthreads();
+      for (int p = tid; p < nrot; p += NT) s_car[p] = ldcg(Rcol(ldcg(I.rslot + q + p)) + q);
+    }
     for (int blk = tm.rank; blk < nblk; blk += tm.size) {
       const int bs = q + blk * DB;
       const int bend = min(bs + DB, np - 1);
@@ -2740,7 +2753,7 @@ struct Engine {
         const int pl = bs + lane;
         const bool act = pl < np - 1;
         const double* col = act ? Rcol(ldcg(I.rslot + pl)) : nullptr;
-        double carry = act ? ldcg(col + q) : 0.0;
+        double carry = act ? (car ? s_car[pl - q] : ldcg(col + q)) : 0.0;
         // the one-FMA form of the block's own steps (below) when every b_e
         // is nonzero and within 2^+-24 (the products of 32 of them stay far
         // inside the FP64 range): Dx = prod_{i < lane} (-b_i)
@@ -2761,7 +2774,7 @@ struct Engine {
         // a time (lanes 0-15 poll cosines, 16-31 sines); the column values
         // are loaded before the wait.  carry = row t of this column after
         // rotations q .. t-1: carry' = -sin carry + cos R(t+1, column).
-        int t = q;
+        int t = car ? bs : q;  // (the one-CTA team's carries are current)
         bool expired = false;
         const long long tw0 = gtimer();
         unsigned spins = 0;
@@ -3017,6 +3030,29 @@ struct Engine {
             }
             if (__shfl_sync(0xffffffffu, bad, 0)) break;
           }
+        }
+      }
+      if (car && bend < np - 1) {
+        // the later positions' row values through this block's rotations:
+        // carry' = -sin carry + cos R(t+1, column), t = bs .. bend-1
+        __syncthreads();
+        if (tid < nown) {
+          s_rc[tid] = ldcg(I.rotc + bs - q + tid);
+          s_rs[tid] = ldcg(I.rots + bs - q + tid);
+        }
+        __syncthreads();
+        for (int p = bend + tid; p < np - 1; p += NT) {
+          const double* col = Rcol(ldcg(I.rslot + p));
+          double c = s_car[p - q];
+          for (int t0 = 0; t0 < nown; t0 += 8) {
+            double bot[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) bot[e] = (t0 + e < nown) ? ldcg(col + bs + 1 + t0 + e) : 0.0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (t0 + e < nown) c = fma(s_rc[t0 + e], bot[e], -s_rs[t0 + e] * c);
+          }
+          s_car[p - q] = c;
         }
       }
     }
